@@ -1,0 +1,151 @@
+"""Seeded synthetic inputs shared by the FP64 oracle and the CUDA path.
+
+This module holds the problem configurations (plain parameter dictionaries,
+named after the workloads they describe) and generators of initial
+macroscopic fields.  It computes no step of the lattice Boltzmann method: it
+only lays out initial shapes (a circular bubble with the hyperbolic-tangent
+interface profile of Sec. 3, a planar interface, a linear wall-to-wall
+temperature, seeded noise) from which each side builds its own populations.
+
+Field arrays are float64 of shape [6, ny, nx] in the order
+phi, u_x, u_y, p, T, psi; node (x, y) sits at [:, y, x].  With walls, rows
+0 and ny-1 are solid and their values are ignored.
+"""
+from __future__ import annotations
+
+import copy
+
+import numpy as np
+
+FIELD_NAMES = ("phi", "ux", "uy", "p", "T", "psi")
+
+# Parameter names, in the order of the C structs of both libraries.
+PARAM_NAMES = (
+    "nx", "ny", "walls", "R", "xb", "yb", "W", "M_phi", "rho_A", "rho_ratio",
+    "mu_ratio", "alpha_ratio", "Re", "Ma", "sigma0", "sigma_T", "sigma_TT",
+    "T_ref", "T_H", "T_C", "beta", "Pi", "Ex", "M_psi", "psi0", "Fext_x",
+    "Fext_y", "gravity", "nu_A", "alpha_A",
+)
+
+# Bubble in a periodic-x channel with a hot wall at y=0 and a cold wall at
+# y=ny-1: 64x128, R=12 at (32, 40), W=4, density ratio 10, viscosity ratio 1,
+# self-rewetting quadratic law sigma_TT=1e-3 (sigma_T=0), sigma0=5e-3,
+# uniform surfactant 0.5, Gibbs elasticity 0.1, Ma=10, Re=1; M_phi=0.1,
+# Pi=8.33, Ex=0.16, M_psi=0.01 as in Sec. 6.
+CHANNEL_64x128 = dict(
+    nx=64, ny=128, walls=1, R=12.0, xb=32.0, yb=40.0, W=4.0, M_phi=0.1,
+    rho_A=1.0, rho_ratio=10.0, mu_ratio=1.0, alpha_ratio=1.0, Re=1.0, Ma=10.0,
+    sigma0=5e-3, sigma_T=0.0, sigma_TT=1e-3, T_ref=0.5, T_H=1.0, T_C=0.0,
+    beta=0.1, Pi=8.33, Ex=0.16, M_psi=0.01, psi0=0.5, Fext_x=0.0, Fext_y=0.0,
+    gravity=0.0, nu_A=0.0, alpha_A=0.0,
+)
+
+# Gibbs elasticity x quadratic sensitivity sweep of the 256x1024 channel.
+SWEEP_BETA = (0.05, 0.1, 0.2)
+SWEEP_SIGMA_TT = (5e-4, 1e-3, 2e-3)
+
+
+def channel_64x128() -> dict:
+    return copy.deepcopy(CHANNEL_64x128)
+
+
+def channel_256x1024(beta: float = 0.1, sigma_TT: float = 1e-3) -> dict:
+    """256x1024 channel, R=32 a quarter of the way along the wall-bounded axis."""
+    p = channel_64x128()
+    p.update(nx=256, ny=1024, R=32.0, xb=128.0, yb=256.0, beta=beta, sigma_TT=sigma_TT)
+    return p
+
+
+def channel_256x1024_sweep() -> list[dict]:
+    return [channel_256x1024(b, s) for b in SWEEP_BETA for s in SWEEP_SIGMA_TT]
+
+
+def channel_1024x4096() -> dict:
+    """1024x4096 channel, R=96, physics of the 64x128 case."""
+    p = channel_64x128()
+    p.update(nx=1024, ny=4096, R=96.0, xb=512.0, yb=1024.0)
+    return p
+
+
+def scaled_channel(nx: int, ny: int) -> dict:
+    """Channel of arbitrary size with the bubble placed like the 64x128 case
+    (R = nx/16*3, centre (nx/2, ny*40/128)); for ragged-size tests."""
+    p = channel_64x128()
+    p.update(nx=int(nx), ny=int(ny), R=max(3.0, 3.0 * nx / 16.0),
+             xb=nx / 2.0, yb=ny * 40.0 / 128.0)
+    return p
+
+
+def _grid(p: dict):
+    y, x = np.mgrid[0:p["ny"], 0:p["nx"]]
+    return x.astype(np.float64), y.astype(np.float64)
+
+
+def linear_wall_temperature(p: dict) -> np.ndarray:
+    """T_H on the wall plane y=1/2, T_C on y=ny-3/2, linear in between."""
+    _, y = _grid(p)
+    if not p["walls"]:
+        return np.full((p["ny"], p["nx"]), float(p["T_ref"]))
+    return p["T_H"] + (p["T_C"] - p["T_H"]) * (y - 0.5) / (p["ny"] - 2.0)
+
+
+def bubble_fields(p: dict, seed: int | None = None, psi_noise: float = 0.0,
+                  u_noise: float = 0.0, T_noise: float = 0.0,
+                  p_noise: float = 0.0) -> np.ndarray:
+    """Circular bubble (phi = 1 inside) of radius R at (xb, yb) with the
+    hyperbolic-tangent interface profile, u = 0, p = 0, linear wall-to-wall T
+    and psi = psi0, plus optional seeded uniform noise on psi, u, T and p."""
+    x, y = _grid(p)
+    r = np.hypot(x - p["xb"], y - p["yb"])
+    out = np.zeros((6, p["ny"], p["nx"]))
+    out[0] = 0.5 + 0.5 * np.tanh(2.0 * (p["R"] - r) / p["W"]) if p["R"] > 0 else 0.0
+    out[4] = linear_wall_temperature(p)
+    out[5] = p["psi0"]
+    if seed is not None:
+        rng = np.random.default_rng(seed)
+        shape = (p["ny"], p["nx"])
+        out[5] += psi_noise * rng.uniform(-1.0, 1.0, shape)
+        out[1] += u_noise * rng.uniform(-1.0, 1.0, shape)
+        out[2] += u_noise * rng.uniform(-1.0, 1.0, shape)
+        out[4] += T_noise * rng.uniform(-1.0, 1.0, shape)
+        out[3] += p_noise * rng.uniform(-1.0, 1.0, shape)
+    if p["walls"]:
+        out[:, 0, :] = 0.0
+        out[:, -1, :] = 0.0
+    return out
+
+
+def slab_fields(p: dict, y1: float, y2: float, psi: float | np.ndarray | None = None,
+                T: float | None = None) -> np.ndarray:
+    """Planar slab of phase B (phi = 1) between y1 and y2 with
+    hyperbolic-tangent interfaces, fluid at rest, uniform T and psi."""
+    _, y = _grid(p)
+    out = np.zeros((6, p["ny"], p["nx"]))
+    W = p["W"]
+    out[0] = 0.5 * (np.tanh(2.0 * (y - y1) / W) - np.tanh(2.0 * (y - y2) / W))
+    out[4] = p["T_ref"] if T is None else T
+    out[5] = p["psi0"] if psi is None else psi
+    return out
+
+
+def uniform_fields(p: dict, phi: float = 0.0, T: float | None = None,
+                   psi: float | None = None, ux: float = 0.0, uy: float = 0.0,
+                   pressure: float = 0.0) -> np.ndarray:
+    out = np.zeros((6, p["ny"], p["nx"]))
+    out[0] = phi
+    out[1] = ux
+    out[2] = uy
+    out[3] = pressure
+    out[4] = p["T_ref"] if T is None else T
+    out[5] = p["psi0"] if psi is None else psi
+    if p["walls"]:
+        out[:, 0, :] = 0.0
+        out[:, -1, :] = 0.0
+    return out
+
+
+def parity_fields(p: dict, seed: int = 0) -> np.ndarray:
+    """Bubble fields with seeded noise on every field, so that every term of
+    the step (velocity-dependent transforms, forces, stencils) is non-zero."""
+    return bubble_fields(p, seed=seed, psi_noise=1e-3, u_noise=1e-3, T_noise=1e-3,
+                         p_noise=1e-5)
