@@ -43,6 +43,15 @@
  *       for T).
  *   R11 L in U_o (Eq. (21)) is the lattice length ny along the temperature
  *       gradient.
+ *   R12 n = grad phi / max(|grad phi|, 1e-4): the paper leaves n undefined
+ *       where grad phi vanishes (the centre of a bubble, where the direction
+ *       of grad phi is arbitrary while theta = 4 phi (1 - phi)/W can still be
+ *       ~1e-2 after internal mixing).  The floor keeps the sharpening flux
+ *       M theta n continuous there.  It only acts where phi (1 - phi) is
+ *       below ~W 1e-4 / 4 on the equilibrium profile; a larger floor would
+ *       make the interface tails diffuse into the bulk (1e-2 fills the bulk
+ *       to phi ~ 4e-3 and slowly dissolves bubbles), a smaller one leaves
+ *       the bubble centre steered by rounding-level gradients.
  */
 #include "lbm_oracle.h"
 
@@ -431,19 +440,17 @@ static void grad_at(const orc_sim* s, field_fn fn, const void* u, int x, int y,
     *gy = ay / CS2;
 }
 
-/* Unit normal n = grad phi / |grad phi| (Sec. 3); 0 where |grad phi| <= 1e-12. */
+/* Unit normal n = grad phi / |grad phi| (Sec. 3), regularised where the
+ * gradient is small (reading R12): n = grad phi / max(|grad phi|, 1e-4). */
+#define ORC_NORMAL_EPS 1e-4
 static void normal_at(const orc_sim* s, int x, int y, double* nx, double* ny)
 {
     double gx, gy;
     grad_at(s, fn_phi, NULL, x, y, &gx, &gy);
     double g = sqrt(gx * gx + gy * gy);
-    if (g > 1e-12) {
-        *nx = gx / g;
-        *ny = gy / g;
-    } else {
-        *nx = 0.0;
-        *ny = 0.0;
-    }
+    if (g < ORC_NORMAL_EPS) g = ORC_NORMAL_EPS;
+    *nx = gx / g;
+    *ny = gy / g;
 }
 
 static double* alloc_d(size_t n)
