@@ -1,0 +1,183 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) implementation of the per-time-step
+ * fused collide-and-stream update of the coupled central-moment lattice
+ * Boltzmann system of Elbousefi, Schupbach, Premnath & Welch, "Investigation
+ * of Surfactant-Laden Bubble Migration Dynamics in Self-Rewetting Fluids
+ * using Lattice Boltzmann Method" (arXiv 2408.00146).
+ *
+ * One simulation ("sim") evolves four D2Q9 distributions on an nx x ny
+ * lattice: f (conservative Allen-Cahn phase field, App. B), g (pressure-based
+ * two-fluid flow with capillary and Marangoni forces, App. C), h (energy,
+ * App. D) and q (surfactant, App. E), coupled through the surface-tension
+ * law sigma(T, psi) of Eq. (6) and the isotropic finite-difference stencils
+ * of Sec. 3.
+ *
+ * Geometry: x is periodic.  With walls != 0, rows y = 0 and y = ny-1 are solid
+ * (halfway bounce-back for f, g, q; anti-bounce-back Dirichlet temperature
+ * T_H at y = 0 and T_C at y = ny-1 for h) and rows 1..ny-2 are fluid; with
+ * walls == 0, y is periodic too.  phi = 0 is the ambient fluid A, phi = 1
+ * the bubble B (Sec. 3).
+ *
+ * Conventions for every call:
+ *   - every entry point returns an lbm_status; nothing aborts or exits;
+ *     on failure lbm_last_error() returns a message for the calling thread;
+ *   - host pointers are read or written before the call returns (the call
+ *     synchronises the sim's stream where it touches host memory); the
+ *     caller keeps ownership of every buffer it passes;
+ *   - device work is issued on the CUDA stream given to lbm_create; calls on
+ *     one sim must not run concurrently from several threads.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_sim lbm_sim;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,    /* invalid argument or parameter out of range       */
+    LBM_ENOMEM = -2,    /* device or host allocation failed / too small     */
+    LBM_ECUDA = -3,     /* a CUDA runtime call failed                       */
+    LBM_EUNSTABLE = -4, /* a NaN or Inf was found by lbm_observe            */
+    LBM_ETIMEOUT = -5,  /* reserved: a bounded device wait gave up          */
+    LBM_ESTATE = -6     /* call out of order (e.g. lbm_step before init)    */
+} lbm_status;
+
+enum { LBM_FP32 = 0 }; /* population storage precision (lbm_params.precision) */
+
+/* Problem parameters, named as in the paper's problem statement (Sec. 2,
+ * Sec. 6).  Lattice units throughout.  The lattice parameters derived from
+ * them are listed under lbm_get_derived. */
+typedef struct {
+    int32_t nx, ny;        /* lattice size; nx periodic axis, ny wall-bounded  */
+    int32_t walls;         /* 1: solid rows y=0, ny-1; 0: periodic y            */
+    double R;              /* bubble radius (length scale of Eq. (8), Eq. (21)) */
+    double xb, yb;         /* bubble centre, used by the analytic initial state */
+    double W;              /* interface width (Sec. 3)                          */
+    double M_phi;          /* ACE mobility, Eq. (12); omega_phi by App. B       */
+    double rho_A;          /* ambient density                                   */
+    double rho_ratio;      /* rho_A / rho_B, Eq. (9)                            */
+    double mu_ratio;       /* mu_A / mu_B, Eq. (9)                              */
+    double alpha_ratio;    /* alpha_A / alpha_B (thermal diffusivities)         */
+    double Re, Ma;         /* Eq. (8) with U = U_o of Eq. (21)                  */
+    double sigma0;         /* surface tension at T_ref, clean interface, Eq. (6)*/
+    double sigma_T;        /* linear sensitivity, Eq. (6) (normal fluids)       */
+    double sigma_TT;       /* quadratic sensitivity, Eq. (6) (self-rewetting)   */
+    double T_ref;          /* reference temperature, Eq. (6)                    */
+    double T_H, T_C;       /* wall temperatures at y = 0 and y = ny-1           */
+    double beta;           /* Gibbs elasticity, Eq. (6)-(7)                     */
+    double Pi, Ex;         /* surfactant groups defined after Eq. (11)          */
+    double M_psi;          /* surfactant diffusivity of the q scheme (App. E)   */
+    double psi0;           /* uniform initial surfactant (analytic init)        */
+    double Fext_x, Fext_y; /* uniform external body force F_ext (Eq. (14))      */
+    double gravity;        /* buoyancy -(rho - rho_A) g along y (Sec. 5.3)      */
+    double nu_A;           /* > 0: ambient kinematic viscosity given directly   */
+    double alpha_A;        /* > 0: ambient thermal diffusivity given directly   */
+    int32_t precision;     /* LBM_FP32                                          */
+} lbm_params;
+
+/* Observables (Sec. 5.3, Sec. 6): phi-weighted bubble centroid ("mass
+ * center") and migration velocity ("average velocity inside the bubble"),
+ * phase-field and surfactant masses, reduced in FP64 over fluid nodes. */
+typedef struct {
+    double t;         /* time steps taken since lbm_init                       */
+    double mass_phi;  /* sum of phi                                            */
+    double mass_psi;  /* sum of psi                                            */
+    double xc, yc;    /* sum(phi x)/sum(phi), sum(phi y)/sum(phi)              */
+    double ux_bub;    /* sum(phi u_x)/sum(phi)                                 */
+    double uy_bub;    /* sum(phi u_y)/sum(phi)                                 */
+    double U_o;       /* characteristic thermocapillary velocity, Eq. (21)     */
+    double t_star;    /* t U_o / R                                             */
+    int32_t nan_flag; /* number of fluid nodes with a non-finite field value   */
+} lbm_obs;
+
+/* Number of doubles written by lbm_get_derived, in this order:
+ * dT, M1, M2, L, U_o, rho_A, rho_B, mu_A, mu_B, nu_A, nu_B, alpha_A, alpha_B,
+ * omega_phi, omega_psi, lambda, s, w, m_psi, D_psi. */
+#define LBM_NDERIVED 20
+
+/* Validates p and writes the LBM_NDERIVED lattice parameters listed above
+ * without creating a sim (host only; no CUDA call).  Errors: LBM_EINVAL. */
+lbm_status lbm_derive(const lbm_params* p, double* out);
+
+/* Bytes of device workspace one sim needs (two population buffers of
+ * 36 floats per node, one field buffer of 6 floats per node, reduction
+ * scratch).  Errors: LBM_EINVAL for invalid parameters. */
+lbm_status lbm_workspace_bytes(const lbm_params* p, size_t* bytes);
+
+/* Creates a sim and allocates its device workspace with cudaMalloc on the
+ * current device.  stream: a cudaStream_t, or NULL for the default stream.
+ * The parameters are validated and the lattice parameters derived as in
+ * Sec. 2 and Sec. 6 (Eqs. (8)-(10), (21); App. B-E relaxation rates); every
+ * relaxation rate must lie in (0, 2), nx >= 4, ny >= 5 with walls (4
+ * without).  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_create(const lbm_params* p, void* stream, lbm_sim** out);
+
+/* As lbm_create, but the caller supplies the device workspace: a pointer
+ * into device memory of at least lbm_workspace_bytes() bytes, 256-byte
+ * aligned, that stays valid and untouched by the caller until lbm_destroy.
+ * The sim never frees it.  Errors: as lbm_create; LBM_ENOMEM if bytes is too
+ * small. */
+lbm_status lbm_create_ex(const lbm_params* p, void* stream, void* workspace,
+                         size_t workspace_bytes, lbm_sim** out);
+
+/* Sets the state at t = 0.
+ *   populations != NULL: host float array [4][9][ny][nx] (sets f, g, h, q;
+ *     directions in the order e_0..e_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),
+ *     (1,1),(-1,1),(-1,-1),(1,-1); wall rows are ignored), copied as the
+ *     post-streaming populations of t = 0;
+ *   else fields != NULL: host double array [6][ny][nx] of phi, u_x, u_y, p,
+ *     T, psi; every population is set to the equilibrium of App. B-E built
+ *     from these fields (n and R from the isotropic stencils of phi);
+ *   else: the analytic state of Sec. 2 -- bubble of radius R at (xb, yb) with
+ *     the tanh profile of Sec. 3, fluid at rest, T linear from T_H on the
+ *     plane y = 1/2 to T_C on y = ny - 3/2 (T_ref without walls), psi = psi0,
+ *     then the equilibria as above.
+ * Errors: LBM_EINVAL (NULL sim), LBM_ECUDA. */
+lbm_status lbm_init(lbm_sim* sim, const double* fields, const float* populations);
+
+/* Advances nsteps time steps: each is one launch of the fused kernel that
+ * streams the populations (Eqs. (27)-(28), (33)-(34), (38)-(39), (43)-(44)
+ * streaming steps), builds phi, T, psi, p* and the forces on a shared-memory
+ * tile with a two-node halo, and collides f, g, h, q.  Asynchronous on the
+ * sim's stream; long runs replay a captured CUDA graph.  nsteps = 0 is a
+ * no-op.  Errors: LBM_EINVAL (nsteps < 0), LBM_ESTATE (not initialised),
+ * LBM_ECUDA. */
+lbm_status lbm_step(lbm_sim* sim, int64_t nsteps);
+
+/* Computes the observables of the current state (out may be NULL) and, if
+ * host_fields != NULL, copies the macroscopic fields phi, u_x, u_y, p, T, psi
+ * into the host double array [6][ny][nx] (wall rows set to 0).  Synchronises
+ * the stream.  Errors: LBM_ESTATE, LBM_ECUDA, LBM_EUNSTABLE if a non-finite
+ * value was found (out and host_fields are still written). */
+lbm_status lbm_observe(lbm_sim* sim, lbm_obs* out, double* host_fields);
+
+/* Copies the current post-streaming populations into the host float array
+ * [4][9][ny][nx] (the layout lbm_init accepts back: checkpoint/restart).
+ * Synchronises the stream.  Errors: LBM_ESTATE, LBM_ECUDA. */
+lbm_status lbm_get_populations(lbm_sim* sim, float* host_pops);
+
+/* Writes the LBM_NDERIVED lattice parameters listed above.  Errors:
+ * LBM_EINVAL. */
+lbm_status lbm_get_derived(const lbm_sim* sim, double* out);
+
+/* Number of kernel launches this sim has issued since creation (every
+ * launch, including those replayed inside CUDA graphs). */
+int64_t lbm_launch_count(const lbm_sim* sim);
+
+/* Frees the sim and, for lbm_create, its workspace.  NULL is a no-op. */
+void lbm_destroy(lbm_sim* sim);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,449 @@
+// lbm_api.cu -- C ABI (include/lbm.h) over the sm_103a kernels: parameter
+// validation and derivation, device workspace, CUDA-graph replay of the step
+// loop, FP64 observables and host transfers.
+#include "lbm.h"
+#include "lbm_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+lbm_status fail(lbm_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+lbm_status fail(lbm_status st, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CUDA_TRY(call)                                                               \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return fail(LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+constexpr double kCs2 = 1.0 / 3.0;
+constexpr int kGraphSteps = 64;  // steps per captured graph (even: buffers return)
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Lattice parameters from the paper's groups (Sec. 2, Sec. 6):
+//  M1 = dT sigma_T / sigma0, M2 = dT^2 sigma_TT / sigma0 (Eq. (10));
+//  U_o = (sigma0 / mu_A)(R / L)(M1 + M2) (Eq. (21)) with mu_A = rho_A nu_A and
+//  nu_A = U_o R / Re (Eq. (8)): U_o = sqrt(sigma0 Re |M1 + M2| / (rho_A L)),
+//  L = ny; alpha_A = U_o R / Ma (Eq. (8)); ratios of Eq. (9);
+//  rates from M = c_s^2 (1/omega - 1/2) (App. B, C, D, E);
+//  lambda = 8 sigma0 Pi / W^2, s = 8 sigma0, w = 4 s / (Ex W^2), m_psi =
+//  D_psi / lambda with D_psi = M_psi (the groups after Eq. (11)).
+lbm_status derive(const lbm_params* p, double* out)
+{
+    if (!p) return fail(LBM_EINVAL, "params is NULL");
+    if (p->precision != LBM_FP32) return fail(LBM_EINVAL, "precision %d unsupported", p->precision);
+    if (p->walls != 0 && p->walls != 1) return fail(LBM_EINVAL, "walls must be 0 or 1");
+    if (p->nx < 4 || p->ny < (p->walls ? 5 : 4))
+        return fail(LBM_EINVAL, "lattice %dx%d too small", p->nx, p->ny);
+    if ((long long)p->nx * p->ny * 36LL > (1LL << 31) - 1)
+        return fail(LBM_EINVAL, "lattice %dx%d too large for 32-bit plane offsets", p->nx, p->ny);
+    if (!(p->rho_A > 0) || !(p->rho_ratio > 0) || !(p->mu_ratio > 0) || !(p->alpha_ratio > 0) ||
+        !(p->W > 0) || !(p->T_ref != 0))
+        return fail(LBM_EINVAL, "rho_A, rho_ratio, mu_ratio, alpha_ratio, W must be > 0, T_ref != 0");
+    if (p->R > 0 && 2 * p->R >= (p->nx < p->ny ? p->nx : p->ny))
+        return fail(LBM_EINVAL, "bubble radius %.3g does not fit the lattice", p->R);
+    const double dT = p->T_H - p->T_C;
+    const double M1 = p->sigma0 != 0 ? dT * p->sigma_T / p->sigma0 : 0.0;
+    const double M2 = p->sigma0 != 0 ? dT * dT * p->sigma_TT / p->sigma0 : 0.0;
+    const double L = (double)p->ny;
+    const double mm = std::fabs(M1 + M2);
+    double U_o, nu_A, alpha_A;
+    if (p->nu_A > 0) {
+        nu_A = p->nu_A;
+        U_o = (p->sigma0 / (p->rho_A * nu_A)) * (p->R / L) * mm;
+    } else {
+        if (!(mm > 0) || !(p->Re > 0) || !(p->R > 0) || !(p->sigma0 > 0))
+            return fail(LBM_EINVAL, "nu_A not given and no thermocapillary velocity scale "
+                                    "(need R, Re, sigma0 > 0 and M1 + M2 != 0)");
+        U_o = std::sqrt(p->sigma0 * p->Re * mm / (p->rho_A * L));
+        nu_A = U_o * p->R / p->Re;
+    }
+    if (p->alpha_A > 0) {
+        alpha_A = p->alpha_A;
+    } else {
+        if (!(U_o > 0) || !(p->Ma > 0))
+            return fail(LBM_EINVAL, "alpha_A not given and Ma or U_o not positive");
+        alpha_A = U_o * p->R / p->Ma;
+    }
+    const double rho_B = p->rho_A / p->rho_ratio;
+    const double mu_A = p->rho_A * nu_A, mu_B = mu_A / p->mu_ratio, nu_B = mu_B / rho_B;
+    const double alpha_B = alpha_A / p->alpha_ratio;
+    const double omega_phi = 1.0 / (p->M_phi / kCs2 + 0.5);
+    const double omega_psi = 1.0 / (p->M_psi / kCs2 + 0.5);
+    const double lambda = p->Pi > 0 ? 8.0 * p->sigma0 * p->Pi / (p->W * p->W) : 0.0;
+    const double s = p->Pi > 0 ? 8.0 * p->sigma0 : 0.0;
+    const double w = (p->Pi > 0 && p->Ex > 0) ? 4.0 * s / (p->Ex * p->W * p->W) : 0.0;
+    const double m_psi = lambda > 0 ? p->M_psi / lambda : 0.0;
+    const double rates[6] = {omega_phi, omega_psi, 1.0 / (nu_A / kCs2 + 0.5),
+                             1.0 / (nu_B / kCs2 + 0.5), 1.0 / (alpha_A / kCs2 + 0.5),
+                             1.0 / (alpha_B / kCs2 + 0.5)};
+    static const char* names[6] = {"omega_phi", "omega_psi", "omega_nu(A)", "omega_nu(B)",
+                                   "omega_T(A)", "omega_T(B)"};
+    for (int i = 0; i < 6; ++i)
+        if (!(rates[i] > 0.0 && rates[i] < 2.0))
+            return fail(LBM_EINVAL, "relaxation rate %s = %g outside (0, 2)", names[i], rates[i]);
+    const double v[LBM_NDERIVED] = {dT,    M1,      M2,        L,         U_o,
+                                    p->rho_A, rho_B, mu_A,     mu_B,      nu_A,
+                                    nu_B,  alpha_A, alpha_B,   omega_phi, omega_psi,
+                                    lambda, s,      w,         m_psi,     p->M_psi};
+    if (out) std::memcpy(out, v, sizeof v);
+    return LBM_OK;
+}
+
+LbmDev make_dev(const lbm_params* p, const double* dv)
+{
+    LbmDev d{};
+    d.nx = p->nx;
+    d.ny = p->ny;
+    d.walls = p->walls;
+    d.y0 = p->walls ? 1 : 0;
+    d.nfy = p->walls ? p->ny - 2 : p->ny;
+    d.W = (float)p->W;
+    d.mphi_4_over_W = (float)(p->M_phi * 4.0 / p->W);
+    d.omega_phi = (float)dv[13];
+    d.omega_psi = (float)dv[14];
+    d.m_psi = (float)dv[18];
+    d.g_s32 = (float)(32.0 * dv[16] / (p->W * p->W));
+    d.g_w = (float)dv[17];
+    d.rhoA = (float)dv[5];
+    d.drho = (float)(dv[6] - dv[5]);
+    d.muA = (float)dv[7];
+    d.dmu = (float)(dv[8] - dv[7]);
+    d.alphaA = (float)dv[11];
+    d.dalpha = (float)(dv[12] - dv[11]);
+    d.sigma0 = (float)p->sigma0;
+    d.s0beta_over_Tref = (float)(p->sigma0 * p->beta / p->T_ref);
+    d.sigma_T = (float)p->sigma_T;
+    d.sigma_TT = (float)p->sigma_TT;
+    d.T_ref = (float)p->T_ref;
+    d.T_H = (float)p->T_H;
+    d.T_C = (float)p->T_C;
+    d.deltas_coef = (float)(1.5 * p->W);
+    d.Fext_x = (float)p->Fext_x;
+    d.Fext_y = (float)p->Fext_y;
+    d.gravity = (float)p->gravity;
+    d.R = (float)p->R;
+    d.xb = (float)p->xb;
+    d.yb = (float)p->yb;
+    d.psi0 = (float)p->psi0;
+    return d;
+}
+
+struct Layout {
+    size_t pop_bytes, fld_bytes, part_bytes, res_bytes, total;
+};
+
+Layout layout_of(const lbm_params* p)
+{
+    Layout L;
+    const size_t N = (size_t)p->nx * p->ny;
+    L.pop_bytes = align256(36 * N * sizeof(float));
+    L.fld_bytes = align256(6 * N * sizeof(float));
+    L.part_bytes = align256((size_t)kReduceBlocks * 8 * sizeof(double));
+    L.res_bytes = align256(16 * sizeof(double));
+    L.total = 2 * L.pop_bytes + L.fld_bytes + L.part_bytes + L.res_bytes;
+    return L;
+}
+
+}  // namespace
+
+struct lbm_sim {
+    lbm_params p;
+    double derived[LBM_NDERIVED];
+    LbmDev dev;
+    cudaStream_t stream;
+    cudaStream_t cap_stream;
+    int device;
+    bool owns_ws;
+    void* ws;
+    size_t ws_bytes;
+    float* pop[2];
+    float* fld;
+    double* part;
+    double* res;
+    int cur;
+    bool ready;
+    int64_t t;
+    int64_t launches;
+    cudaGraph_t graph;
+    cudaGraphExec_t graph_exec;
+    float* h_stage;  // pinned, 6 N floats
+    double* h_res;   // pinned, 16 doubles
+};
+
+static lbm_status create_impl(const lbm_params* p, void* stream, void* ws, size_t ws_bytes,
+                              bool owns, lbm_sim** out)
+{
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    double dv[LBM_NDERIVED];
+    lbm_status st = derive(p, dv);
+    if (st != LBM_OK) return st;
+    Layout L = layout_of(p);
+    if (!owns && ws_bytes < L.total)
+        return fail(LBM_ENOMEM, "workspace of %zu bytes < %zu needed", ws_bytes, L.total);
+    if (!owns && (reinterpret_cast<uintptr_t>(ws) & 255u))
+        return fail(LBM_EINVAL, "workspace must be 256-byte aligned");
+    lbm_sim* s = new (std::nothrow) lbm_sim();
+    if (!s) return fail(LBM_ENOMEM, "host allocation failed");
+    s->p = *p;
+    std::memcpy(s->derived, dv, sizeof dv);
+    s->dev = make_dev(p, dv);
+    s->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) {
+        delete s;
+        return fail(LBM_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    }
+    if (owns) {
+        e = cudaMalloc(&ws, L.total);
+        if (e != cudaSuccess) {
+            delete s;
+            return fail(LBM_ENOMEM, "cudaMalloc(%zu): %s", L.total, cudaGetErrorString(e));
+        }
+        ws_bytes = L.total;
+    }
+    s->owns_ws = owns;
+    s->ws = ws;
+    s->ws_bytes = ws_bytes;
+    char* base = static_cast<char*>(ws);
+    s->pop[0] = reinterpret_cast<float*>(base);
+    s->pop[1] = reinterpret_cast<float*>(base + L.pop_bytes);
+    s->fld = reinterpret_cast<float*>(base + 2 * L.pop_bytes);
+    s->part = reinterpret_cast<double*>(base + 2 * L.pop_bytes + L.fld_bytes);
+    s->res = reinterpret_cast<double*>(base + 2 * L.pop_bytes + L.fld_bytes + L.part_bytes);
+    e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s->h_res), 16 * sizeof(double));
+    if (e != cudaSuccess) {
+        lbm_destroy(s);
+        return fail(LBM_ECUDA, "stream/pinned setup: %s", cudaGetErrorString(e));
+    }
+    *out = s;
+    return LBM_OK;
+}
+
+extern "C" {
+
+lbm_status lbm_derive(const lbm_params* p, double* out)
+{
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    return derive(p, out);
+}
+
+lbm_status lbm_workspace_bytes(const lbm_params* p, size_t* bytes)
+{
+    if (!bytes) return fail(LBM_EINVAL, "bytes is NULL");
+    lbm_status st = derive(p, nullptr);
+    if (st != LBM_OK) return st;
+    *bytes = layout_of(p).total;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_params* p, void* stream, lbm_sim** out)
+{
+    return create_impl(p, stream, nullptr, 0, true, out);
+}
+
+lbm_status lbm_create_ex(const lbm_params* p, void* stream, void* workspace,
+                         size_t workspace_bytes, lbm_sim** out)
+{
+    if (!workspace) return fail(LBM_EINVAL, "workspace is NULL");
+    return create_impl(p, stream, workspace, workspace_bytes, false, out);
+}
+
+void lbm_destroy(lbm_sim* s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    else cudaDeviceSynchronize();
+    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->h_stage) cudaFreeHost(s->h_stage);
+    if (s->h_res) cudaFreeHost(s->h_res);
+    if (s->owns_ws && s->ws) cudaFree(s->ws);
+    delete s;
+}
+
+const char* lbm_last_error(void) { return g_err; }
+
+lbm_status lbm_get_derived(const lbm_sim* s, double* out)
+{
+    if (!s || !out) return fail(LBM_EINVAL, "NULL argument");
+    std::memcpy(out, s->derived, sizeof s->derived);
+    return LBM_OK;
+}
+
+int64_t lbm_launch_count(const lbm_sim* s) { return s ? s->launches : 0; }
+
+static lbm_status ensure_stage(lbm_sim* s)
+{
+    if (s->h_stage) return LBM_OK;
+    const size_t N = (size_t)s->p.nx * s->p.ny;
+    CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&s->h_stage), 6 * N * sizeof(float)));
+    return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_sim* s, const double* fields, const float* populations)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    const size_t N = (size_t)s->p.nx * s->p.ny;
+    s->ready = false;
+    s->cur = 0;
+    s->t = 0;
+    if (populations) {
+        CUDA_TRY(cudaMemcpyAsync(s->pop[0], populations, 36 * N * sizeof(float),
+                                 cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        s->ready = true;
+        return LBM_OK;
+    }
+    CUDA_TRY(cudaMemsetAsync(s->pop[0], 0, 36 * N * sizeof(float), s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->pop[1], 0, 36 * N * sizeof(float), s->stream));
+    if (fields) {
+        lbm_status st = ensure_stage(s);
+        if (st != LBM_OK) return st;
+        CUDA_TRY(cudaStreamSynchronize(s->stream));  // staging buffer free
+        for (size_t i = 0; i < 6 * N; ++i) s->h_stage[i] = (float)fields[i];
+        CUDA_TRY(cudaMemcpyAsync(s->fld, s->h_stage, 6 * N * sizeof(float),
+                                 cudaMemcpyHostToDevice, s->stream));
+    } else {
+        CUDA_TRY(launch_analytic_fields(s->dev, s->fld, s->stream));
+        s->launches += 1;
+    }
+    CUDA_TRY(launch_init_equilibrium(s->dev, s->fld, s->pop[0], s->stream));
+    s->launches += 1;
+    if (fields) CUDA_TRY(cudaStreamSynchronize(s->stream));
+    s->ready = true;
+    return LBM_OK;
+}
+
+static lbm_status build_graph(lbm_sim* s)
+{
+    // The capture stream waits for nothing: the graph holds only kernels
+    // whose inputs are the workspace buffers.
+    CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < kGraphSteps; ++i) {
+        cudaError_t e = launch_step(s->dev, s->pop[i & 1], s->pop[(i + 1) & 1], s->cap_stream);
+        if (e != cudaSuccess) {
+            cudaGraph_t g;
+            cudaStreamEndCapture(s->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            return fail(LBM_ECUDA, "capture: %s", cudaGetErrorString(e));
+        }
+    }
+    CUDA_TRY(cudaStreamEndCapture(s->cap_stream, &s->graph));
+    CUDA_TRY(cudaGraphInstantiate(&s->graph_exec, s->graph, 0));
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_sim* s, int64_t nsteps)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+    if (!s->ready) return fail(LBM_ESTATE, "lbm_step before lbm_init");
+    int64_t left = nsteps;
+    if (left >= kGraphSteps + 1 || (left >= kGraphSteps && s->cur == 0)) {
+        if (!s->graph_exec) {
+            lbm_status st = build_graph(s);
+            if (st != LBM_OK) return st;
+        }
+        if (s->cur == 1) {
+            CUDA_TRY(launch_step(s->dev, s->pop[1], s->pop[0], s->stream));
+            s->cur = 0;
+            --left;
+            s->launches += 1;
+        }
+        while (left >= kGraphSteps) {
+            CUDA_TRY(cudaGraphLaunch(s->graph_exec, s->stream));
+            left -= kGraphSteps;
+            s->launches += kGraphSteps;
+        }
+    }
+    for (; left > 0; --left) {
+        CUDA_TRY(launch_step(s->dev, s->pop[s->cur], s->pop[s->cur ^ 1], s->stream));
+        s->cur ^= 1;
+        s->launches += 1;
+    }
+    s->t += nsteps;
+    return LBM_OK;
+}
+
+lbm_status lbm_observe(lbm_sim* s, lbm_obs* out, double* host_fields)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (!s->ready) return fail(LBM_ESTATE, "lbm_observe before lbm_init");
+    const size_t N = (size_t)s->p.nx * s->p.ny;
+    CUDA_TRY(launch_fields(s->dev, s->pop[s->cur], s->fld, s->stream));
+    CUDA_TRY(launch_observe_reduce(s->dev, s->fld, s->part, kReduceBlocks, s->res, s->stream));
+    s->launches += 3;
+    CUDA_TRY(cudaMemcpyAsync(s->h_res, s->res, 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                             s->stream));
+    if (host_fields) {
+        lbm_status st = ensure_stage(s);
+        if (st != LBM_OK) return st;
+        CUDA_TRY(cudaMemcpyAsync(s->h_stage, s->fld, 6 * N * sizeof(float),
+                                 cudaMemcpyDeviceToHost, s->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (host_fields) {
+        const int nx = s->p.nx, ny = s->p.ny;
+        for (int k = 0; k < 6; ++k)
+            for (int y = 0; y < ny; ++y) {
+                const bool fluid = !s->p.walls || (y >= 1 && y <= ny - 2);
+                const size_t o = (size_t)k * N + (size_t)y * nx;
+                for (int x = 0; x < nx; ++x)
+                    host_fields[o + x] = fluid ? (double)s->h_stage[o + x] : 0.0;
+            }
+    }
+    const double* r = s->h_res;
+    const double m = r[0];
+    if (out) {
+        out->t = (double)s->t;
+        out->mass_phi = m;
+        out->mass_psi = r[1];
+        out->xc = m != 0 ? r[2] / m : 0.0;
+        out->yc = m != 0 ? r[3] / m : 0.0;
+        out->ux_bub = m != 0 ? r[4] / m : 0.0;
+        out->uy_bub = m != 0 ? r[5] / m : 0.0;
+        out->U_o = s->derived[4];
+        out->t_star = s->p.R > 0 ? (double)s->t * s->derived[4] / s->p.R : 0.0;
+        out->nan_flag = (int32_t)r[6];
+    }
+    if (r[6] != 0.0 || !std::isfinite(m))
+        return fail(LBM_EUNSTABLE, "%.0f fluid nodes hold non-finite values at t = %lld", r[6],
+                    (long long)s->t);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_sim* s, float* host_pops)
+{
+    if (!s || !host_pops) return fail(LBM_EINVAL, "NULL argument");
+    if (!s->ready) return fail(LBM_ESTATE, "lbm_get_populations before lbm_init");
+    const size_t N = (size_t)s->p.nx * s->p.ny;
+    CUDA_TRY(cudaMemcpyAsync(host_pops, s->pop[s->cur], 36 * N * sizeof(float),
+                             cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,46 @@
+// lbm_internal.h -- device-side parameter block and launch wrappers shared by
+// the C-ABI layer (lbm_api.cu) and the kernels (lbm_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// Lattice parameters in the form the kernels use them (FP32), derived on the
+// host from lbm_params (Sec. 2, Sec. 6, App. B-E).
+struct LbmDev {
+    int nx, ny, walls;
+    int y0;    // first fluid row (1 with walls, 0 without)
+    int nfy;   // number of fluid rows
+    // phase field (App. B): kappa_eq,10 = M_phi theta n_x, theta = 4 phi(1-phi)/W
+    float W, mphi_4_over_W, omega_phi;
+    // surfactant (App. E): rate, adsorption-flux coefficient m_psi and the
+    // derivative of the Eq. (5) bracket G'(phi) = (phi - 1/2)(c_s32 phi(1-phi) + w)
+    float omega_psi, m_psi, g_s32, g_w;
+    // property interpolation, Eq. (17) (phi_A = 0, phi_B = 1)
+    float rhoA, drho, muA, dmu, alphaA, dalpha;
+    // surface tension law, Eq. (6)
+    float sigma0, s0beta_over_Tref, sigma_T, sigma_TT, T_ref;
+    float T_H, T_C;
+    // CSF: delta_s = 1.5 W |grad phi|^2 (Sec. 3)
+    float deltas_coef;
+    float Fext_x, Fext_y, gravity;
+    // analytic initial state
+    float R, xb, yb, psi0;
+};
+
+// Tile shape of the fused step kernel.
+constexpr int kTileX = 32;
+constexpr int kTileY = 8;
+
+cudaError_t launch_step(const LbmDev& d, const float* src, float* dst, cudaStream_t s);
+cudaError_t launch_fields(const LbmDev& d, const float* src, float* fields, cudaStream_t s);
+cudaError_t launch_analytic_fields(const LbmDev& d, float* fields, cudaStream_t s);
+cudaError_t launch_init_equilibrium(const LbmDev& d, const float* fields, float* pops,
+                                    cudaStream_t s);
+// FP64 reduction of the observables over fluid nodes into result[0..7]:
+// sum phi, sum psi, sum phi x, sum phi y, sum phi u_x, sum phi u_y,
+// non-finite count, fluid node count.  partials holds nblocks * 8 doubles.
+cudaError_t launch_observe_reduce(const LbmDev& d, const float* fields, double* partials,
+                                  int nblocks, double* result, cudaStream_t s);
+constexpr int kReduceBlocks = 304;  // 2 x 152 SMs
+constexpr int kReduceThreads = 256;

@@ -1,0 +1,630 @@
+// lbm_kernels.cu -- sm_103a kernels of the fused collide-and-stream step of
+// the coupled central-moment lattice Boltzmann system of arXiv 2408.00146.
+//
+// Data layout in HBM (structure of arrays, x fastest):
+//   populations  pop[set][alpha][y][x], set 0 = f (phase field, App. B),
+//                1 = g (pressure/velocity, App. C), 2 = h (energy, App. D),
+//                3 = q (surfactant, App. E); FP32; two buffers (ping-pong);
+//   fields       fld[k][y][x], k = phi, u_x, u_y, p, T, psi; FP32.
+// A buffer holds the post-streaming populations of one time level.  One step
+// reads them at the node (coalesced), computes the macroscopic fields of the
+// tile plus a two-node halo in shared memory, evaluates the isotropic
+// stencils, forces and the four central-moment collisions in registers, and
+// pushes the post-collision populations to the neighbours of the other
+// buffer (halfway bounce-back / anti-bounce-back at the walls).
+//
+// The moment transforms use the factorised form of the binomial frame change
+// of Eq. (24b)/(46): central moments are taken first along x, then along y,
+// and the inverse runs the same one-dimensional maps backwards.  Each
+// collision is applied as an increment: the change of the central moments is
+// mapped back to the populations and added to them, which keeps the conserved
+// zeroth moments to one rounding per population instead of re-synthesising the
+// populations from a rounded sum.
+#include "lbm_internal.h"
+
+#include <math.h>
+
+namespace {
+
+constexpr float kCs2 = 1.0f / 3.0f;
+constexpr float kW0 = 4.0f / 9.0f, kW1 = 1.0f / 9.0f, kW2 = 1.0f / 36.0f;
+// n = grad phi / max(|grad phi|, eps): the normal of Sec. 3 is undefined where
+// grad phi vanishes (bubble interiors, whose centre has no gradient direction);
+// the floor keeps the sharpening flux M theta n there proportional to grad phi
+// instead of following rounding noise.  It acts only where phi (1 - phi) <
+// W eps / 4 on the equilibrium profile (the far tails of the interface).
+constexpr float kNormalEps = 1e-4f;
+
+// D2Q9 velocity set (App. B; e_8 = (1,-1) as in the second row of P).
+__device__ __forceinline__ int ex_of(int a)
+{
+    return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
+}
+__device__ __forceinline__ int ey_of(int a)
+{
+    return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
+}
+__device__ __forceinline__ int opp_of(int a)
+{
+    return a == 0 ? 0 : (a <= 4 ? ((a + 1) & 3) + 1 : ((a - 3) & 3) + 5);
+}
+__device__ __forceinline__ float w_of(int a) { return a == 0 ? kW0 : (a <= 4 ? kW1 : kW2); }
+
+__device__ __forceinline__ int wrap(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// Source row of a stencil value at physical row y, and which wall image it is
+// (-1 bottom, +1 top, 0 none): with walls, rows at and beyond a wall mirror
+// about the wall plane (y = 1/2, y = ny - 3/2); without walls y wraps.
+__device__ __forceinline__ int src_row(const LbmDev& d, int y, int& side)
+{
+    side = 0;
+    if (!d.walls) return wrap(y, d.ny);
+    if (y < 1) {
+        side = -1;
+        y = 1 - y;
+    } else if (y > d.ny - 2) {
+        side = 1;
+        y = 2 * d.ny - 3 - y;
+    }
+    // positions farther than one reflection only feed inactive tile slots
+    return min(max(y, 1), d.ny - 2);
+}
+
+// Surface tension law, Eq. (6); ln(1 - psi) with psi clamped to [0, 1-1e-6].
+__device__ __forceinline__ float sigma_eos(const LbmDev& d, float T, float psi)
+{
+    float pc = fminf(fmaxf(psi, 0.0f), 1.0f - 1e-6f);
+    float dT = T - d.T_ref;
+    return d.sigma0 + d.s0beta_over_Tref * T * log1pf(-pc) + d.sigma_T * dT +
+           d.sigma_TT * dT * dT;
+}
+
+// Isotropic gradient 3 sum_a w_a e_a X(x + e_a) on a shared-memory array
+// (row index = y).
+template <int P>
+__device__ __forceinline__ void grad_smem(const float (*a)[P], int r, int c, float& gx, float& gy)
+{
+    const float e = a[r][c + 1], w = a[r][c - 1], n = a[r + 1][c], s = a[r - 1][c];
+    const float ne = a[r + 1][c + 1], nw = a[r + 1][c - 1], se = a[r - 1][c + 1],
+                sw = a[r - 1][c - 1];
+    gx = (1.0f / 3.0f) * (e - w) + (1.0f / 12.0f) * ((ne - nw) + (se - sw));
+    gy = (1.0f / 3.0f) * (n - s) + (1.0f / 12.0f) * ((ne - se) + (nw - sw));
+}
+
+// Inverse of the factorised central-moment transform: central moments
+// c_mn (m along x, n along y) about (ux, uy) to the nine populations.
+__device__ __forceinline__ void central_to_pop(float c00, float c10, float c01, float c20,
+                                               float c02, float c11, float c21, float c12,
+                                               float c22, float ux, float uy, float out[9])
+{
+    const float uy2 = uy * uy, ux2 = ux * ux;
+    // along y: (c_m0, c_m1, c_m2) -> partial x-moments k_m at e_y = -1, 0, +1
+    float k0m, k00, k0p, k1m, k10, k1p, k2m, k20, k2p;
+#define YPASS(a0, a1, a2, km, kz, kp)                                       \
+    kz = (a0) * (1.0f - uy2) - 2.0f * uy * (a1) - (a2);                     \
+    kp = 0.5f * ((a0) * (uy2 + uy) + (a1) * (2.0f * uy + 1.0f) + (a2));     \
+    km = 0.5f * ((a0) * (uy2 - uy) + (a1) * (2.0f * uy - 1.0f) + (a2));
+    YPASS(c00, c01, c02, k0m, k00, k0p)
+    YPASS(c10, c11, c12, k1m, k10, k1p)
+    YPASS(c20, c21, c22, k2m, k20, k2p)
+#undef YPASS
+    // along x at each e_y: (k_0, k_1, k_2) -> populations at e_x = -1, 0, +1
+#define XPASS(a0, a1, a2, fm, fz, fp)                                       \
+    fz = (a0) * (1.0f - ux2) - 2.0f * ux * (a1) - (a2);                     \
+    fp = 0.5f * ((a0) * (ux2 + ux) + (a1) * (2.0f * ux + 1.0f) + (a2));     \
+    fm = 0.5f * ((a0) * (ux2 - ux) + (a1) * (2.0f * ux - 1.0f) + (a2));
+    XPASS(k00, k10, k20, out[3], out[0], out[1])   // e_y = 0
+    XPASS(k0p, k1p, k2p, out[6], out[2], out[5])   // e_y = +1
+    XPASS(k0m, k1m, k2m, out[7], out[4], out[8])   // e_y = -1
+#undef XPASS
+}
+
+// Equilibrium-type scalar scheme (f, h, q): post-collision central moments
+// (s, a, b, s/3, s/3, 0, 0, 0, s/9).
+__device__ __forceinline__ void scalar_post(float s, float a, float b, float ux, float uy,
+                                            float out[9])
+{
+    central_to_pop(s, a, b, kCs2 * s, kCs2 * s, 0.0f, 0.0f, 0.0f, kCs2 * kCs2 * s, ux, uy,
+                   out);
+}
+
+// Forward factorised transform: populations to the nine central moments about
+// (ux, uy), first along x at each e_y, then along y; c[] in the order
+// 00, 10, 01, 20, 02, 11, 21, 12, 22.
+__device__ __forceinline__ void pop_to_central(const float f[9], float ux, float uy, float c[9])
+{
+    float k0[3], k1[3], k2[3];  // index 0: e_y = -1, 1: e_y = 0, 2: e_y = +1
+#define XFWD(fm, fz, fp, j)                                   \
+    {                                                         \
+        const float d = (fp) - (fm), s = (fp) + (fm);         \
+        k0[j] = s + (fz);                                     \
+        k1[j] = d - ux * k0[j];                               \
+        k2[j] = s - ux * (d + k1[j]);                         \
+    }
+    XFWD(f[7], f[4], f[8], 0)
+    XFWD(f[3], f[0], f[1], 1)
+    XFWD(f[6], f[2], f[5], 2)
+#undef XFWD
+#define YFWD(k, c0, c1, c2)                                   \
+    {                                                         \
+        const float d = k[2] - k[0], s = k[2] + k[0];         \
+        c0 = s + k[1];                                        \
+        c1 = d - uy * c0;                                     \
+        c2 = s - uy * (d + c1);                               \
+    }
+    YFWD(k0, c[0], c[2], c[4])
+    YFWD(k1, c[1], c[5], c[7])
+    YFWD(k2, c[3], c[6], c[8])
+#undef YFWD
+}
+
+// Adds to the populations the change of their central moments: f += P^-1
+// F(-u) dc, i.e. the collision applied as an increment, so that the zeroth
+// moment is carried by the stored populations rather than re-synthesised from
+// its rounded sum.
+__device__ __forceinline__ void add_central_increment(float f[9], const float dc[9], float ux,
+                                                      float uy)
+{
+    float df[9];
+    central_to_pop(dc[0], dc[1], dc[2], dc[3], dc[4], dc[5], dc[6], dc[7], dc[8], ux, uy, df);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) f[a] += df[a];
+}
+
+// Collision of a scalar scheme (App. B, D, E): zeroth moment kept, first-order
+// central moments relaxed with rate w towards (e10, e01), every higher moment
+// set to its equilibrium (s/3, s/3, 0, 0, 0, s/9).
+__device__ __forceinline__ void scalar_collide(float f[9], float s, float e10, float e01, float w,
+                                               float ux, float uy)
+{
+    float c[9];
+    pop_to_central(f, ux, uy, c);
+    float dc[9];
+    dc[0] = 0.0f;
+    dc[1] = w * (e10 - c[1]);
+    dc[2] = w * (e01 - c[2]);
+    dc[3] = kCs2 * s - c[3];
+    dc[4] = kCs2 * s - c[4];
+    dc[5] = -c[5];
+    dc[6] = -c[6];
+    dc[7] = -c[7];
+    dc[8] = kCs2 * kCs2 * s - c[8];
+    add_central_increment(f, dc, ux, uy);
+}
+
+__device__ __forceinline__ void load9(const float* __restrict__ base, size_t N, int idx,
+                                      float v[9])
+{
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = __ldg(base + (size_t)a * N + idx);
+}
+
+__device__ __forceinline__ float sum9(const float v[9])
+{
+    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+}
+__device__ __forceinline__ float mx9(const float v[9])
+{
+    return (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
+}
+__device__ __forceinline__ float my9(const float v[9])
+{
+    return (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+}
+
+// Push the nine post-collision populations of node (x, y) of one set to the
+// neighbours in dst; a population headed into a wall row returns to the node
+// in the opposite direction (halfway bounce-back, or anti-bounce-back with
+// the wall temperature for the energy set).
+template <bool kEnergy>
+__device__ __forceinline__ void push_store(const LbmDev& d, float* __restrict__ dst, size_t N,
+                                           int x, int y, const float v[9])
+{
+    const int xe = (x + 1 == d.nx) ? 0 : x + 1;
+    const int xw = (x == 0) ? d.nx - 1 : x - 1;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const int ex = ex_of(a), ey = ey_of(a);
+        int ty = y + ey;
+        float val = v[a];
+        int plane = a, tx = ex > 0 ? xe : (ex < 0 ? xw : x);
+        if (d.walls && (ty == 0 || ty == d.ny - 1)) {
+            plane = opp_of(a);
+            tx = x;
+            if (kEnergy) val = -val + 2.0f * w_of(a) * (ty == 0 ? d.T_H : d.T_C);
+            ty = y;
+        } else if (!d.walls) {
+            ty = (ty < 0) ? d.ny - 1 : (ty == d.ny ? 0 : ty);
+        }
+        dst[(size_t)plane * N + (size_t)ty * d.nx + tx] = val;
+    }
+}
+
+enum Mode { kStep = 0, kFields = 1 };
+
+// The fused step.  Block = kTileX x kTileY threads, one output node each.
+template <int kMode>
+__global__ void __launch_bounds__(kTileX * kTileY, 2)
+    step_kernel(LbmDev d, const float* __restrict__ src, float* __restrict__ dst)
+{
+    constexpr int TX = kTileX, TY = kTileY;
+    constexpr int EW = TX + 4, EH = TY + 4;   // phi tile with a 2-node halo
+    constexpr int RW = TX + 2, RH = TY + 2;   // other fields, 1-node halo
+    __shared__ float s_phi[EH][EW];
+    __shared__ float s_sig[RH][RW];
+    __shared__ float s_phs[RH][RW];
+    __shared__ float s_nx[RH][RW];
+    __shared__ float s_ny[RH][RW];
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * TX + tx;
+    const int x0 = blockIdx.x * TX;
+    const int fy0 = blockIdx.y * TY;          // tile origin in fluid-row numbering
+    const size_t N = (size_t)d.nx * d.ny;
+    const float* __restrict__ F = src;
+    const float* __restrict__ G = src + 9 * N;
+    const float* __restrict__ H = src + 18 * N;
+    const float* __restrict__ Q = src + 27 * N;
+
+    const int gx = x0 + tx;
+    const int gfy = fy0 + ty;
+    const bool active = (gx < d.nx) && (gfy < d.nfy);
+    const int gy = d.y0 + gfy;
+
+    // ---- tile fields: own node ---------------------------------------------
+    float f[9], g[9], h[9], q[9];
+    float phi, T, psi, pst;
+    {
+        int side;
+        const int sx = wrap(gx, d.nx);
+        const int sy = src_row(d, gy, side);
+        const int idx = sy * d.nx + sx;
+        load9(F, N, idx, f);
+        load9(G, N, idx, g);
+        load9(H, N, idx, h);
+        load9(Q, N, idx, q);
+        phi = sum9(f);
+        pst = sum9(g);
+        T = sum9(h);
+        psi = sum9(q);
+        float Tg = T;
+        if (side < 0) Tg = 2.0f * d.T_H - T;
+        if (side > 0) Tg = 2.0f * d.T_C - T;
+        s_phi[ty + 2][tx + 2] = phi;
+        s_sig[ty + 1][tx + 1] = sigma_eos(d, Tg, psi);
+        s_phs[ty + 1][tx + 1] = pst - (d.rhoA + phi * d.drho) * kCs2;
+    }
+    // ---- halo ----------------------------------------------------------------
+    for (int i = tid; i < EW * EH; i += TX * TY) {
+        const int ex = i % EW, ey = i / EW;
+        if (ex >= 2 && ex < TX + 2 && ey >= 2 && ey < TY + 2) continue;
+        const bool ring1 = ex >= 1 && ex <= TX + 2 && ey >= 1 && ey <= TY + 2;
+        int side;
+        const int sx = wrap(x0 + ex - 2, d.nx);
+        const int sy = src_row(d, d.y0 + fy0 + ey - 2, side);
+        const int idx = sy * d.nx + sx;
+        float v[9];
+        load9(F, N, idx, v);
+        const float ph = sum9(v);
+        s_phi[ey][ex] = ph;
+        if (ring1) {
+            load9(G, N, idx, v);
+            const float ps = sum9(v);
+            load9(H, N, idx, v);
+            float Th = sum9(v);
+            load9(Q, N, idx, v);
+            const float sp = sum9(v);
+            if (side < 0) Th = 2.0f * d.T_H - Th;
+            if (side > 0) Th = 2.0f * d.T_C - Th;
+            s_sig[ey - 1][ex - 1] = sigma_eos(d, Th, sp);
+            s_phs[ey - 1][ex - 1] = ps - (d.rhoA + ph * d.drho) * kCs2;
+        }
+    }
+    __syncthreads();
+    // ---- unit normals n = grad phi / |grad phi| on tile + 1-node halo -----------
+    for (int i = tid; i < RW * RH; i += TX * TY) {
+        const int cx = i % RW, cy = i / RW;
+        float gxp, gyp;
+        grad_smem<EW>(s_phi, cy + 1, cx + 1, gxp, gyp);
+        const float inv = 1.0f / fmaxf(sqrtf(gxp * gxp + gyp * gyp), kNormalEps);
+        s_nx[cy][cx] = gxp * inv;
+        s_ny[cy][cx] = gyp * inv;
+    }
+    __syncthreads();
+    if (!active) return;
+
+    // ---- stencils, forces, velocity, pressure (Sec. 3, App. C) --------------------
+    const int r = ty + 1, c = tx + 1;
+    float gpx, gpy;
+    grad_smem<EW>(s_phi, ty + 2, tx + 2, gpx, gpy);
+    const float g2 = gpx * gpx + gpy * gpy;
+    const float n_x = s_nx[r][c], n_y = s_ny[r][c];
+    float dnx_dx, dnx_dy, dny_dx, dny_dy;
+    grad_smem<RW>(s_nx, r, c, dnx_dx, dnx_dy);
+    grad_smem<RW>(s_ny, r, c, dny_dx, dny_dy);
+    const float kappa = dnx_dx + dny_dy;
+    float sgx, sgy, phx, phy;
+    grad_smem<RW>(s_sig, r, c, sgx, sgy);
+    grad_smem<RW>(s_phs, r, c, phx, phy);
+    const float sig = s_sig[r][c];
+    const float ndots = n_x * sgx + n_y * sgy;
+    const float deltas = d.deltas_coef * g2;
+    const float rho = d.rhoA + phi * d.drho;
+    const float inv_rho = 1.0f / rho;
+    const float Ftx = deltas * (-sig * kappa * n_x + sgx - n_x * ndots) + d.Fext_x;
+    const float Fty = deltas * (-sig * kappa * n_y + sgy - n_y * ndots) + d.Fext_y -
+                      (rho - d.rhoA) * d.gravity;
+    const float Fpx = -phx, Fpy = -phy;
+    const float jx = mx9(g), jy = my9(g);
+    const float ux = (3.0f * jx + 0.5f * Ftx) * inv_rho;
+    const float uy = (3.0f * jy + 0.5f * Fty) * inv_rho;
+    const float Gam = Fpx * ux + Fpy * uy;
+    const float p = pst + 0.5f * Gam;
+
+    if (kMode == kFields) {
+        const size_t o = (size_t)gy * d.nx + gx;
+        dst[o] = phi;
+        dst[N + o] = ux;
+        dst[2 * N + o] = uy;
+        dst[3 * N + o] = p;
+        dst[4 * N + o] = T;
+        dst[5 * N + o] = psi;
+        return;
+    }
+
+    // ---- f: conservative Allen-Cahn (App. B) ---------------------------------------
+    {
+        const float theta_m = d.mphi_4_over_W * phi * (1.0f - phi);   // M_phi theta
+        scalar_collide(f, phi, theta_m * n_x, theta_m * n_y, d.omega_phi, ux, uy);
+        push_store<false>(d, dst, N, gx, gy, f);
+    }
+    // ---- h: energy (App. D), rate from the local thermal diffusivity -----------------
+    {
+        const float alpha = d.alphaA + phi * d.dalpha;
+        const float wT = 1.0f / (3.0f * alpha + 0.5f);
+        scalar_collide(h, T, 0.0f, 0.0f, wT, ux, uy);
+        push_store<true>(d, dst + 18 * N, N, gx, gy, h);
+    }
+    // ---- q: surfactant (App. E) -------------------------------------------------
+    {
+        const float dG = (phi - 0.5f) * (d.g_s32 * phi * (1.0f - phi) + d.g_w);
+        const float flux = -d.m_psi * psi * (1.0f - psi) * dG;   // times grad phi
+        scalar_collide(q, psi, flux * gpx, flux * gpy, d.omega_psi, ux, uy);
+        push_store<false>(d, dst + 27 * N, N, gx, gy, q);
+    }
+    // ---- g: two-fluid pressure/velocity (App. C) ----------------------------------------
+    {
+        const float mu = d.muA + phi * d.dmu;
+        const float wn = 1.0f / (3.0f * mu * inv_rho + 0.5f);
+        const float vp = p - rho * kCs2;                      // varphi = p - rho c_s^2
+        const float ux2 = ux * ux, uy2 = uy * uy;
+        float c[9];
+        pop_to_central(g, ux, uy, c);
+        // equilibria (Eq. (31)) and sources (Eq. (32))
+        const float e20 = p * kCs2 + vp * ux2, e02 = p * kCs2 + vp * uy2;
+        const float e11 = vp * ux * uy;
+        const float e21 = -vp * (ux2 + kCs2) * uy;
+        const float e12 = -vp * (uy2 + kCs2) * ux;
+        // c_s^6 rho + varphi (u_x^2 + c_s^2)(u_y^2 + c_s^2) with the two O(rho)
+        // terms cancelled exactly: p c_s^4 + varphi (c_s^2 (u_x^2 + u_y^2) + u_x^2 u_y^2)
+        const float e22 = kCs2 * kCs2 * p + vp * (kCs2 * (ux2 + uy2) + ux2 * uy2);
+        const float s10 = kCs2 * Ftx - ux * Gam, s01 = kCs2 * Fty - uy * Gam;
+        const float s20 = 2.0f * kCs2 * Fpx * ux + (ux2 + kCs2) * Gam;
+        const float s02 = 2.0f * kCs2 * Fpy * uy + (uy2 + kCs2) * Gam;
+        const float s11 = kCs2 * (Fpx * uy + Fpy * ux) + ux * uy * Gam;
+        // relaxation (Eq. (33)) as an increment of the central moments: rate 1
+        // for 00, 10, 01, 2s, 21, 12, 22 (new value = equilibrium + source/2),
+        // omega_nu for 2d and 11.  With rate 1 the zeroth and first moments
+        // change by exactly their source: the equilibrium p + Gam/2 and
+        // -varphi u + s/2 differ from the pre-collision p* and j - u p* by
+        // Gam/2 and s/2, by the definitions of p and u (Eq. (34)).
+        float dc[9];
+        dc[0] = Gam;
+        dc[1] = s10;
+        dc[2] = s01;
+        const float d2s = (e20 + e02) + 0.5f * (s20 + s02) - (c[3] + c[4]);
+        const float k2d = c[3] - c[4];
+        const float d2d = wn * ((e20 - e02) - k2d) + (1.0f - 0.5f * wn) * (s20 - s02);
+        dc[3] = 0.5f * (d2s + d2d);
+        dc[4] = 0.5f * (d2s - d2d);
+        dc[5] = wn * (e11 - c[5]) + (1.0f - 0.5f * wn) * s11;
+        dc[6] = e21 - c[6];
+        dc[7] = e12 - c[7];
+        dc[8] = e22 - c[8];
+        add_central_increment(g, dc, ux, uy);
+        push_store<false>(d, dst + 9 * N, N, gx, gy, g);
+    }
+}
+
+// Equilibrium populations of every fluid node from the macroscopic fields
+// (initial state): P^-1 F(-u) applied to the equilibria of Eqs. (26), (31),
+// (37), (42), with n and R from the isotropic stencil of phi.
+__global__ void init_equilibrium_kernel(LbmDev d, const float* __restrict__ fld,
+                                        float* __restrict__ pops)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int fy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= d.nx || fy >= d.nfy) return;
+    const int y = d.y0 + fy;
+    const size_t N = (size_t)d.nx * d.ny;
+    auto phi_at = [&](int xx, int yy) {
+        int side;
+        const int sy = src_row(d, yy, side);
+        return fld[(size_t)sy * d.nx + wrap(xx, d.nx)];
+    };
+    float gx = (1.0f / 3.0f) * (phi_at(x + 1, y) - phi_at(x - 1, y)) +
+               (1.0f / 12.0f) * ((phi_at(x + 1, y + 1) - phi_at(x - 1, y + 1)) +
+                                 (phi_at(x + 1, y - 1) - phi_at(x - 1, y - 1)));
+    float gy = (1.0f / 3.0f) * (phi_at(x, y + 1) - phi_at(x, y - 1)) +
+               (1.0f / 12.0f) * ((phi_at(x + 1, y + 1) - phi_at(x + 1, y - 1)) +
+                                 (phi_at(x - 1, y + 1) - phi_at(x - 1, y - 1)));
+    const float inv = 1.0f / fmaxf(sqrtf(gx * gx + gy * gy), kNormalEps);
+    const size_t o = (size_t)y * d.nx + x;
+    const float phi = fld[o], ux = fld[N + o], uy = fld[2 * N + o], p = fld[3 * N + o];
+    const float T = fld[4 * N + o], psi = fld[5 * N + o];
+    float out[9];
+    const float theta_m = d.mphi_4_over_W * phi * (1.0f - phi);
+    scalar_post(phi, theta_m * gx * inv, theta_m * gy * inv, ux, uy, out);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) pops[(size_t)a * N + o] = out[a];
+    const float rho = d.rhoA + phi * d.drho;
+    const float vp = p - rho * kCs2;
+    const float ux2 = ux * ux, uy2 = uy * uy;
+    central_to_pop(p, -vp * ux, -vp * uy, p * kCs2 + vp * ux2, p * kCs2 + vp * uy2,
+                   vp * ux * uy, -vp * (ux2 + kCs2) * uy, -vp * (uy2 + kCs2) * ux,
+                   kCs2 * kCs2 * p + vp * (kCs2 * (ux2 + uy2) + ux2 * uy2), ux, uy, out);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) pops[(size_t)(9 + a) * N + o] = out[a];
+    scalar_post(T, 0.0f, 0.0f, ux, uy, out);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) pops[(size_t)(18 + a) * N + o] = out[a];
+    const float dG = (phi - 0.5f) * (d.g_s32 * phi * (1.0f - phi) + d.g_w);
+    const float flux = -d.m_psi * psi * (1.0f - psi) * dG;
+    scalar_post(psi, flux * gx, flux * gy, ux, uy, out);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) pops[(size_t)(27 + a) * N + o] = out[a];
+}
+
+// Analytic initial fields: tanh bubble (Sec. 3 profile), fluid at rest, T
+// linear between the wall planes, uniform psi.
+__global__ void analytic_fields_kernel(LbmDev d, float* __restrict__ fld)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= d.nx || y >= d.ny) return;
+    const size_t N = (size_t)d.nx * d.ny;
+    const size_t o = (size_t)y * d.nx + x;
+    float phi = 0.0f;
+    if (d.R > 0.0f) {
+        const float r = hypotf((float)x - d.xb, (float)y - d.yb);
+        phi = 0.5f + 0.5f * tanhf(2.0f * (d.R - r) / d.W);
+    }
+    float T = d.T_ref;
+    if (d.walls) T = d.T_H + (d.T_C - d.T_H) * ((float)y - 0.5f) / (float)(d.ny - 2);
+    const bool fluid = !d.walls || (y >= 1 && y <= d.ny - 2);
+    fld[o] = fluid ? phi : 0.0f;
+    fld[N + o] = 0.0f;
+    fld[2 * N + o] = 0.0f;
+    fld[3 * N + o] = 0.0f;
+    fld[4 * N + o] = fluid ? T : 0.0f;
+    fld[5 * N + o] = fluid ? d.psi0 : 0.0f;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// FP64 block sums of the observables; fixed grid and order: deterministic.
+__global__ void __launch_bounds__(kReduceThreads)
+    observe_partial_kernel(LbmDev d, const float* __restrict__ fld, double* __restrict__ part)
+{
+    constexpr int K = 8;
+    double acc[K] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const size_t N = (size_t)d.nx * d.ny;
+    const long long total = (long long)d.nx * d.nfy;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % d.nx);
+        const int y = d.y0 + (int)(i / d.nx);
+        const size_t o = (size_t)y * d.nx + x;
+        const float phi = fld[o], ux = fld[N + o], uy = fld[2 * N + o], p = fld[3 * N + o];
+        const float T = fld[4 * N + o], psi = fld[5 * N + o];
+        const bool bad = !(isfinite(phi) && isfinite(ux) && isfinite(uy) && isfinite(p) &&
+                           isfinite(T) && isfinite(psi));
+        acc[0] += (double)phi;
+        acc[1] += (double)psi;
+        acc[2] += (double)phi * x;
+        acc[3] += (double)phi * y;
+        acc[4] += (double)phi * ux;
+        acc[5] += (double)phi * uy;
+        acc[6] += bad ? 1.0 : 0.0;
+        acc[7] += 1.0;
+    }
+    __shared__ double sm[kReduceThreads / 32][K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sm[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) s += sm[w][threadIdx.x];
+        part[(size_t)blockIdx.x * K + threadIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kReduceThreads)
+    observe_final_kernel(const double* __restrict__ part, int nblocks, double* __restrict__ out)
+{
+    constexpr int K = 8;
+    __shared__ double sm[kReduceThreads / 32][K];
+    double acc[K] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] += part[(size_t)b * K + k];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sm[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) s += sm[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+dim3 step_grid(const LbmDev& d)
+{
+    return dim3((d.nx + kTileX - 1) / kTileX, (d.nfy + kTileY - 1) / kTileY);
+}
+
+}  // namespace
+
+cudaError_t launch_step(const LbmDev& d, const float* src, float* dst, cudaStream_t s)
+{
+    step_kernel<kStep><<<step_grid(d), dim3(kTileX, kTileY), 0, s>>>(d, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields(const LbmDev& d, const float* src, float* fields, cudaStream_t s)
+{
+    step_kernel<kFields><<<step_grid(d), dim3(kTileX, kTileY), 0, s>>>(d, src, fields);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_analytic_fields(const LbmDev& d, float* fields, cudaStream_t s)
+{
+    dim3 b(32, 8), g((d.nx + 31) / 32, (d.ny + 7) / 8);
+    analytic_fields_kernel<<<g, b, 0, s>>>(d, fields);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_equilibrium(const LbmDev& d, const float* fields, float* pops,
+                                    cudaStream_t s)
+{
+    dim3 b(32, 8), g((d.nx + 31) / 32, (d.nfy + 7) / 8);
+    init_equilibrium_kernel<<<g, b, 0, s>>>(d, fields, pops);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observe_reduce(const LbmDev& d, const float* fields, double* partials,
+                                  int nblocks, double* result, cudaStream_t s)
+{
+    observe_partial_kernel<<<nblocks, kReduceThreads, 0, s>>>(d, fields, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    observe_final_kernel<<<1, kReduceThreads, 0, s>>>(partials, nblocks, result);
+    return cudaGetLastError();
+}
