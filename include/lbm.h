@@ -177,6 +177,34 @@ void lbm_destroy(lbm_sim* sim);
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* lbm_last_error(void);
 
+/* FP64 observable sums over the fluid nodes of a caller-provided device field
+ * array, for callers that cannot allocate device memory where they call it:
+ * code recording a stream into a CUDA graph, latency-critical loops that must
+ * not take the device-wide synchronisation of cudaMalloc/cudaFree, and hosts
+ * whose device memory is fully budgeted in advance.  The paper has no
+ * counterpart: it is plumbing around the reduction lbm_observe performs.
+ *   d_fields: device float array [6][ny][nx] (phi, u_x, u_y, p, T, psi; the
+ *     layout lbm_observe copies out), read only; with walls != 0 rows 0 and
+ *     ny-1 are skipped.
+ *   d_sums: device double array of 8, written: sum phi, sum psi, sum phi x,
+ *     sum phi y, sum phi u_x, sum phi u_y, number of nodes holding a
+ *     non-finite value, number of fluid nodes.
+ *   stream: cudaStream_t (NULL = default stream); the call only enqueues two
+ *     kernels and returns without synchronising.
+ * No allocation: the block partial sums live in a fixed 256 KiB array inside
+ * the library's device image, present on every device that loads the
+ * library until the process exits.  That caps the lattice at 16,777,216
+ * fluid nodes; larger ones return LBM_EINVAL with a message saying so.  The
+ * first call on a device looks the array's device address up (a host-side
+ * runtime query, no allocation); make that first call before any stream
+ * capture.  Every call shares the one array, so calls whose kernels overlap
+ * on the GPU (different streams without ordering) race and return garbage;
+ * order them on one stream or with events.  Each call writes every partial
+ * it reads, so nothing has to be cleared between calls.
+ * Errors: LBM_EINVAL, LBM_ECUDA (message in lbm_last_error()). */
+lbm_status lbm_reduce_observables_noalloc(const float* d_fields, int32_t nx, int32_t ny,
+                                          int32_t walls, double* d_sums, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

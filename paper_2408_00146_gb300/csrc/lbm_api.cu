@@ -166,6 +166,12 @@ Layout layout_of(const lbm_params* p)
 
 }  // namespace
 
+lbm_status lbm_set_error(lbm_status st, const char* msg)
+{
+    snprintf(g_err, sizeof g_err, "%s", msg);
+    return st;
+}
+
 struct lbm_sim {
     lbm_params p;
     double derived[LBM_NDERIVED];

@@ -5,6 +5,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lbm.h"
+
+// Records msg as the calling thread's lbm_last_error() text and returns st.
+__attribute__((visibility("hidden"))) lbm_status lbm_set_error(lbm_status st, const char* msg);
+
 // Lattice parameters in the form the kernels use them (FP32), derived on the
 // host from lbm_params (Sec. 2, Sec. 6, App. B-E).
 struct LbmDev {

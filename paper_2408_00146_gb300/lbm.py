@@ -52,7 +52,7 @@ STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA"
 EXPORTS = [
     "lbm_derive", "lbm_workspace_bytes", "lbm_create", "lbm_create_ex", "lbm_init", "lbm_step",
     "lbm_observe", "lbm_get_populations", "lbm_get_derived", "lbm_launch_count",
-    "lbm_destroy", "lbm_last_error",
+    "lbm_destroy", "lbm_last_error", "lbm_reduce_observables_noalloc",
 ]
 
 
@@ -100,6 +100,8 @@ def load() -> ctypes.CDLL:
             L.lbm_launch_count.restype = ctypes.c_int64
             L.lbm_destroy.argtypes = [vp]
             L.lbm_destroy.restype = None
+            L.lbm_reduce_observables_noalloc.argtypes = [vp, ctypes.c_int32, ctypes.c_int32,
+                                                         ctypes.c_int32, vp, vp]
             L.lbm_last_error.argtypes = []
             L.lbm_last_error.restype = ctypes.c_char_p
             for name in EXPORTS:
@@ -210,6 +212,16 @@ def lbm_launch_count(sim) -> int:
 
 def lbm_destroy(sim):
     load().lbm_destroy(sim)
+
+
+def lbm_reduce_observables_noalloc(d_fields_ptr: int, nx: int, ny: int, walls: int,
+                                   d_sums_ptr: int, stream=None):
+    """Observable sums of a device field array into a device array of 8
+    doubles, without any device allocation (see include/lbm.h)."""
+    _check(load().lbm_reduce_observables_noalloc(
+        ctypes.c_void_p(d_fields_ptr), int(nx), int(ny), int(walls),
+        ctypes.c_void_p(d_sums_ptr), ctypes.c_void_p(_stream_handle(stream))),
+        "lbm_reduce_observables_noalloc")
 
 
 # ---- convenience object ---------------------------------------------------------------
