@@ -194,7 +194,49 @@ struct lbm_sim {
     cudaGraphExec_t graph_exec;
     float* h_stage;  // pinned, 6 N floats
     double* h_res;   // pinned, 16 doubles
+    int* err;        // device flag: a bounded wait in a kernel gave up
+    bool have_tmap;  // TMA descriptors of both population buffers are valid
+    CUtensorMap tmap[2];
 };
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// TMA descriptors of the population tensors [36][ny][nx] (FP32), box
+// {kTileX, kTileY, 36}.  TMA needs 16-byte row strides, i.e. nx % 4 == 0;
+// otherwise (or if the driver lacks the entry point) every tile is staged
+// with per-thread loads instead.
+bool encode_population_maps(lbm_sim* s)
+{
+    if (s->p.nx % 4 != 0) return false;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+    EncodeTiledFn encode = reinterpret_cast<EncodeTiledFn>(fn);
+    const cuuint64_t dims[3] = {(cuuint64_t)s->p.nx, (cuuint64_t)s->p.ny, 36};
+    const cuuint64_t strides[2] = {(cuuint64_t)s->p.nx * sizeof(float),
+                                   (cuuint64_t)s->p.nx * s->p.ny * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)kTileX, (cuuint32_t)kTileY, 36};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    for (int b = 0; b < 2; ++b) {
+        CUresult r = encode(&s->tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->pop[b], dims, strides,
+                            box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    return true;
+}
+
+const CUtensorMap* map_of(const lbm_sim* s, int buf) { return s->have_tmap ? &s->tmap[buf] : nullptr; }
+
+}  // namespace
 
 static lbm_status create_impl(const lbm_params* p, void* stream, void* ws, size_t ws_bytes,
                               bool owns, lbm_sim** out)
@@ -237,6 +279,8 @@ static lbm_status create_impl(const lbm_params* p, void* stream, void* ws, size_
     s->fld = reinterpret_cast<float*>(base + 2 * L.pop_bytes);
     s->part = reinterpret_cast<double*>(base + 2 * L.pop_bytes + L.fld_bytes);
     s->res = reinterpret_cast<double*>(base + 2 * L.pop_bytes + L.fld_bytes + L.part_bytes);
+    s->err = reinterpret_cast<int*>(s->res + 12);
+    s->have_tmap = encode_population_maps(s);
     e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s->h_res), 16 * sizeof(double));
     if (e != cudaSuccess) {
@@ -317,6 +361,7 @@ lbm_status lbm_init(lbm_sim* s, const double* fields, const float* populations)
     s->cur = 0;
     s->t = 0;
     if (populations) {
+        CUDA_TRY(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
         CUDA_TRY(cudaMemcpyAsync(s->pop[0], populations, 36 * N * sizeof(float),
                                  cudaMemcpyHostToDevice, s->stream));
         CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -325,6 +370,7 @@ lbm_status lbm_init(lbm_sim* s, const double* fields, const float* populations)
     }
     CUDA_TRY(cudaMemsetAsync(s->pop[0], 0, 36 * N * sizeof(float), s->stream));
     CUDA_TRY(cudaMemsetAsync(s->pop[1], 0, 36 * N * sizeof(float), s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
     if (fields) {
         lbm_status st = ensure_stage(s);
         if (st != LBM_OK) return st;
@@ -349,7 +395,8 @@ static lbm_status build_graph(lbm_sim* s)
     // whose inputs are the workspace buffers.
     CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kGraphSteps; ++i) {
-        cudaError_t e = launch_step(s->dev, s->pop[i & 1], s->pop[(i + 1) & 1], s->cap_stream);
+        cudaError_t e = launch_step(s->dev, s->pop[i & 1], s->pop[(i + 1) & 1], map_of(s, i & 1),
+                                    s->err, s->cap_stream);
         if (e != cudaSuccess) {
             cudaGraph_t g;
             cudaStreamEndCapture(s->cap_stream, &g);
@@ -374,7 +421,7 @@ lbm_status lbm_step(lbm_sim* s, int64_t nsteps)
             if (st != LBM_OK) return st;
         }
         if (s->cur == 1) {
-            CUDA_TRY(launch_step(s->dev, s->pop[1], s->pop[0], s->stream));
+            CUDA_TRY(launch_step(s->dev, s->pop[1], s->pop[0], map_of(s, 1), s->err, s->stream));
             s->cur = 0;
             --left;
             s->launches += 1;
@@ -386,7 +433,8 @@ lbm_status lbm_step(lbm_sim* s, int64_t nsteps)
         }
     }
     for (; left > 0; --left) {
-        CUDA_TRY(launch_step(s->dev, s->pop[s->cur], s->pop[s->cur ^ 1], s->stream));
+        CUDA_TRY(launch_step(s->dev, s->pop[s->cur], s->pop[s->cur ^ 1], map_of(s, s->cur), s->err,
+                             s->stream));
         s->cur ^= 1;
         s->launches += 1;
     }
@@ -399,10 +447,10 @@ lbm_status lbm_observe(lbm_sim* s, lbm_obs* out, double* host_fields)
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     if (!s->ready) return fail(LBM_ESTATE, "lbm_observe before lbm_init");
     const size_t N = (size_t)s->p.nx * s->p.ny;
-    CUDA_TRY(launch_fields(s->dev, s->pop[s->cur], s->fld, s->stream));
+    CUDA_TRY(launch_fields(s->dev, s->pop[s->cur], s->fld, map_of(s, s->cur), s->err, s->stream));
     CUDA_TRY(launch_observe_reduce(s->dev, s->fld, s->part, kReduceBlocks, s->res, s->stream));
     s->launches += 3;
-    CUDA_TRY(cudaMemcpyAsync(s->h_res, s->res, 8 * sizeof(double), cudaMemcpyDeviceToHost,
+    CUDA_TRY(cudaMemcpyAsync(s->h_res, s->res, 13 * sizeof(double), cudaMemcpyDeviceToHost,
                              s->stream));
     if (host_fields) {
         lbm_status st = ensure_stage(s);
@@ -435,6 +483,10 @@ lbm_status lbm_observe(lbm_sim* s, lbm_obs* out, double* host_fields)
         out->t_star = s->p.R > 0 ? (double)s->t * s->derived[4] / s->p.R : 0.0;
         out->nan_flag = (int32_t)r[6];
     }
+    int timed_out = 0;
+    std::memcpy(&timed_out, r + 12, sizeof(int));
+    if (timed_out)
+        return fail(LBM_ETIMEOUT, "a kernel gave up waiting for a tile copy; results are invalid");
     if (r[6] != 0.0 || !std::isfinite(m))
         return fail(LBM_EUNSTABLE, "%.0f fluid nodes hold non-finite values at t = %lld", r[6],
                     (long long)s->t);

@@ -2,6 +2,7 @@
 // the C-ABI layer (lbm_api.cu) and the kernels (lbm_kernels.cu).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,8 +38,13 @@ struct LbmDev {
 constexpr int kTileX = 32;
 constexpr int kTileY = 8;
 
-cudaError_t launch_step(const LbmDev& d, const float* src, float* dst, cudaStream_t s);
-cudaError_t launch_fields(const LbmDev& d, const float* src, float* fields, cudaStream_t s);
+// tmap: TMA descriptor of the population tensor [36][ny][nx] at src (box
+// {kTileX, kTileY, 36}), or NULL to stage every tile with per-thread loads.
+// err: device flag set to 1 if a bounded wait for a tile copy gave up.
+cudaError_t launch_step(const LbmDev& d, const float* src, float* dst, const CUtensorMap* tmap,
+                        int* err, cudaStream_t s);
+cudaError_t launch_fields(const LbmDev& d, const float* src, float* fields, const CUtensorMap* tmap,
+                          int* err, cudaStream_t s);
 cudaError_t launch_analytic_fields(const LbmDev& d, float* fields, cudaStream_t s);
 cudaError_t launch_init_equilibrium(const LbmDev& d, const float* fields, float* pops,
                                     cudaStream_t s);

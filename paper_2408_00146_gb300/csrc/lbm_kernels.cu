@@ -22,33 +22,19 @@
 // populations from a rounded sum.
 #include "lbm_internal.h"
 
+#include <cuda.h>
 #include <math.h>
 
 namespace {
 
 constexpr float kCs2 = 1.0f / 3.0f;
-constexpr float kW0 = 4.0f / 9.0f, kW1 = 1.0f / 9.0f, kW2 = 1.0f / 36.0f;
+constexpr float kW1 = 1.0f / 9.0f, kW2 = 1.0f / 36.0f;  // D2Q9 weights of axis and diagonal links
 // n = grad phi / max(|grad phi|, eps): the normal of Sec. 3 is undefined where
 // grad phi vanishes (bubble interiors, whose centre has no gradient direction);
 // the floor keeps the sharpening flux M theta n there proportional to grad phi
 // instead of following rounding noise.  It acts only where phi (1 - phi) <
 // W eps / 4 on the equilibrium profile (the far tails of the interface).
 constexpr float kNormalEps = 1e-4f;
-
-// D2Q9 velocity set (App. B; e_8 = (1,-1) as in the second row of P).
-__device__ __forceinline__ int ex_of(int a)
-{
-    return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
-}
-__device__ __forceinline__ int ey_of(int a)
-{
-    return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
-}
-__device__ __forceinline__ int opp_of(int a)
-{
-    return a == 0 ? 0 : (a <= 4 ? ((a + 1) & 3) + 1 : ((a - 3) & 3) + 5);
-}
-__device__ __forceinline__ float w_of(int a) { return a == 0 ? kW0 : (a <= 4 ? kW1 : kW2); }
 
 __device__ __forceinline__ int wrap(int v, int n)
 {
@@ -196,13 +182,6 @@ __device__ __forceinline__ void scalar_collide(float f[9], float s, float e10, f
     add_central_increment(f, dc, ux, uy);
 }
 
-__device__ __forceinline__ void load9(const float* __restrict__ base, size_t N, int idx,
-                                      float v[9])
-{
-#pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = __ldg(base + (size_t)a * N + idx);
-}
-
 __device__ __forceinline__ float sum9(const float v[9])
 {
     return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
@@ -216,107 +195,209 @@ __device__ __forceinline__ float my9(const float v[9])
     return (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
 }
 
-// Push the nine post-collision populations of node (x, y) of one set to the
-// neighbours in dst; a population headed into a wall row returns to the node
-// in the opposite direction (halfway bounce-back, or anti-bounce-back with
-// the wall temperature for the energy set).
-template <bool kEnergy>
-__device__ __forceinline__ void push_store(const LbmDev& d, float* __restrict__ dst, size_t N,
-                                           int x, int y, const float v[9])
+enum Mode { kStep = 0, kFields = 1 };
+
+// ---- TMA / mbarrier helpers (sm_90+ PTX) -------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
-    const int xe = (x + 1 == d.nx) ? 0 : x + 1;
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after kMaxWaitPolls polls (each poll may suspend the
+// thread for a short hardware-chosen interval) instead of spinning forever.
+constexpr int kMaxWaitPolls = 1 << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    for (int i = 0; i < kMaxWaitPolls; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// One TMA copy of the box {kTileX, kTileY, 36} at (x, y, plane 0) of the
+// population tensor [36][ny][nx] into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                              uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(0), "r"(bar)
+        : "memory");
+}
+
+// Neighbour offsets (within one population plane) of node idx = y*nx + x,
+// x wrapping periodically and y wrapping without walls.
+struct Nbr {
+    int o[9];
+};
+
+__device__ __forceinline__ Nbr neighbours(const LbmDev& d, int x, int y)
+{
     const int xw = (x == 0) ? d.nx - 1 : x - 1;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        const int ex = ex_of(a), ey = ey_of(a);
-        int ty = y + ey;
-        float val = v[a];
-        int plane = a, tx = ex > 0 ? xe : (ex < 0 ? xw : x);
-        if (d.walls && (ty == 0 || ty == d.ny - 1)) {
-            plane = opp_of(a);
-            tx = x;
-            if (kEnergy) val = -val + 2.0f * w_of(a) * (ty == 0 ? d.T_H : d.T_C);
-            ty = y;
-        } else if (!d.walls) {
-            ty = (ty < 0) ? d.ny - 1 : (ty == d.ny ? 0 : ty);
-        }
-        dst[(size_t)plane * N + (size_t)ty * d.nx + tx] = val;
+    const int xe = (x + 1 == d.nx) ? 0 : x + 1;
+    const int r = y * d.nx;
+    int rs = r - d.nx, rn = r + d.nx;
+    if (!d.walls) {
+        if (y == 0) rs = (d.ny - 1) * d.nx;
+        if (y == d.ny - 1) rn = 0;
+    }
+    Nbr n;
+    n.o[0] = r + x;
+    n.o[1] = r + xe;
+    n.o[2] = rn + x;
+    n.o[3] = r + xw;
+    n.o[4] = rs + x;
+    n.o[5] = rn + xe;
+    n.o[6] = rn + xw;
+    n.o[7] = rs + xw;
+    n.o[8] = rs + xe;
+    return n;
+}
+
+// Push the nine post-collision populations of one set to the neighbours in
+// dst_set (plane stride N).  wall = -1 (bottom fluid row), +1 (top fluid row)
+// or 0; a population headed into a wall row returns to the node in the
+// opposite direction (halfway bounce-back, or anti-bounce-back with the wall
+// temperature Tw for the energy set).  wall is uniform across a warp.
+template <bool kEnergy>
+__device__ __forceinline__ void store_set(float* __restrict__ dst_set, int N, const Nbr& nb,
+                                          const float v[9], int wall, float Tw)
+{
+    const int o0 = nb.o[0];
+    dst_set[o0] = v[0];
+    dst_set[N + nb.o[1]] = v[1];
+    dst_set[3 * N + nb.o[3]] = v[3];
+    if (wall == 0) {
+        dst_set[2 * N + nb.o[2]] = v[2];
+        dst_set[4 * N + nb.o[4]] = v[4];
+        dst_set[5 * N + nb.o[5]] = v[5];
+        dst_set[6 * N + nb.o[6]] = v[6];
+        dst_set[7 * N + nb.o[7]] = v[7];
+        dst_set[8 * N + nb.o[8]] = v[8];
+    } else if (wall < 0) {  // e_y = -1 hits the bottom wall: 4 -> 2, 7 -> 5, 8 -> 6
+        dst_set[2 * N + nb.o[2]] = v[2];
+        dst_set[5 * N + nb.o[5]] = v[5];
+        dst_set[6 * N + nb.o[6]] = v[6];
+        dst_set[2 * N + o0] = kEnergy ? -v[4] + 2.0f * kW1 * Tw : v[4];
+        dst_set[5 * N + o0] = kEnergy ? -v[7] + 2.0f * kW2 * Tw : v[7];
+        dst_set[6 * N + o0] = kEnergy ? -v[8] + 2.0f * kW2 * Tw : v[8];
+    } else {                // e_y = +1 hits the top wall: 2 -> 4, 5 -> 7, 6 -> 8
+        dst_set[4 * N + nb.o[4]] = v[4];
+        dst_set[7 * N + nb.o[7]] = v[7];
+        dst_set[8 * N + nb.o[8]] = v[8];
+        dst_set[4 * N + o0] = kEnergy ? -v[2] + 2.0f * kW1 * Tw : v[2];
+        dst_set[7 * N + o0] = kEnergy ? -v[5] + 2.0f * kW2 * Tw : v[5];
+        dst_set[8 * N + o0] = kEnergy ? -v[6] + 2.0f * kW2 * Tw : v[6];
     }
 }
 
-enum Mode { kStep = 0, kFields = 1 };
+// Wrapped column of x for lattices at least as wide as a tile plus its halo;
+// narrower lattices take the modulo.
+__device__ __forceinline__ int wrap_x(const LbmDev& d, int x)
+{
+    if (d.nx >= kTileX + 4) return x < 0 ? x + d.nx : (x >= d.nx ? x - d.nx : x);
+    return wrap(x, d.nx);
+}
 
 // The fused step.  Block = kTileX x kTileY threads, one output node each.
-template <int kMode>
-__global__ void __launch_bounds__(kTileX * kTileY, 2)
-    step_kernel(LbmDev d, const float* __restrict__ src, float* __restrict__ dst)
+// The tile's own populations are staged in shared memory: by one TMA copy for
+// tiles that lie wholly inside the lattice (kTma: the tensor map of src is
+// valid), else by per-thread loads that also resolve periodic images and
+// wall mirrors for the slots past the lattice edge.
+template <int kMode, bool kTma>
+__global__ void __launch_bounds__(kTileX * kTileY, 3)
+    step_kernel(LbmDev d, const float* __restrict__ src, float* __restrict__ dst,
+                const __grid_constant__ CUtensorMap tmap, int* __restrict__ err)
 {
     constexpr int TX = kTileX, TY = kTileY;
     constexpr int EW = TX + 4, EH = TY + 4;   // phi tile with a 2-node halo
     constexpr int RW = TX + 2, RH = TY + 2;   // other fields, 1-node halo
+    __shared__ __align__(128) float s_pop[36][TY][TX];
     __shared__ float s_phi[EH][EW];
     __shared__ float s_sig[RH][RW];
     __shared__ float s_phs[RH][RW];
     __shared__ float s_nx[RH][RW];
     __shared__ float s_ny[RH][RW];
+    __shared__ __align__(8) uint64_t s_bar;
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX;
     const int fy0 = blockIdx.y * TY;          // tile origin in fluid-row numbering
-    const size_t N = (size_t)d.nx * d.ny;
-    const float* __restrict__ F = src;
-    const float* __restrict__ G = src + 9 * N;
-    const float* __restrict__ H = src + 18 * N;
-    const float* __restrict__ Q = src + 27 * N;
+    const int N = d.nx * d.ny;
 
     const int gx = x0 + tx;
     const int gfy = fy0 + ty;
     const bool active = (gx < d.nx) && (gfy < d.nfy);
     const int gy = d.y0 + gfy;
+    const bool use_tma = kTma && (x0 + TX <= d.nx) && (fy0 + TY <= d.nfy);
+    const uint32_t bar = smem_addr(&s_bar);
 
-    // ---- tile fields: own node ---------------------------------------------
-    float f[9], g[9], h[9], q[9];
-    float phi, T, psi, pst;
-    {
-        int side;
-        const int sx = wrap(gx, d.nx);
-        const int sy = src_row(d, gy, side);
-        const int idx = sy * d.nx + sx;
-        load9(F, N, idx, f);
-        load9(G, N, idx, g);
-        load9(H, N, idx, h);
-        load9(Q, N, idx, q);
-        phi = sum9(f);
-        pst = sum9(g);
-        T = sum9(h);
-        psi = sum9(q);
-        float Tg = T;
-        if (side < 0) Tg = 2.0f * d.T_H - T;
-        if (side > 0) Tg = 2.0f * d.T_C - T;
-        s_phi[ty + 2][tx + 2] = phi;
-        s_sig[ty + 1][tx + 1] = sigma_eos(d, Tg, psi);
-        s_phs[ty + 1][tx + 1] = pst - (d.rhoA + phi * d.drho) * kCs2;
+    // ---- own-node populations into shared memory ------------------------------------
+    int own_side = 0;
+    if (use_tma) {
+        if (tid == 0) mbar_init(bar, 1);
+        __syncthreads();
+        if (tid == 0) {
+            mbar_expect_tx(bar, 36u * TX * TY * sizeof(float));
+            tma_load_tile(smem_addr(&s_pop[0][0][0]), &tmap, x0, d.y0 + fy0, bar);
+        }
+    } else {
+        const int sx = wrap_x(d, gx);
+        const int sy = src_row(d, gy, own_side);
+        const float* p = src + (sy * d.nx + sx);
+#pragma unroll
+        for (int a = 0; a < 36; ++a) s_pop[a][ty][tx] = __ldg(p + a * N);
     }
-    // ---- halo ----------------------------------------------------------------
+
+    // ---- halo fields (plain loads, overlapping the tile copy) -----------------------
     for (int i = tid; i < EW * EH; i += TX * TY) {
         const int ex = i % EW, ey = i / EW;
         if (ex >= 2 && ex < TX + 2 && ey >= 2 && ey < TY + 2) continue;
         const bool ring1 = ex >= 1 && ex <= TX + 2 && ey >= 1 && ey <= TY + 2;
         int side;
-        const int sx = wrap(x0 + ex - 2, d.nx);
+        const int sx = wrap_x(d, x0 + ex - 2);
         const int sy = src_row(d, d.y0 + fy0 + ey - 2, side);
-        const int idx = sy * d.nx + sx;
+        const float* p = src + (sy * d.nx + sx);
         float v[9];
-        load9(F, N, idx, v);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = __ldg(p + a * N);
         const float ph = sum9(v);
         s_phi[ey][ex] = ph;
         if (ring1) {
-            load9(G, N, idx, v);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) v[a] = __ldg(p + (9 + a) * N);
             const float ps = sum9(v);
-            load9(H, N, idx, v);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) v[a] = __ldg(p + (18 + a) * N);
             float Th = sum9(v);
-            load9(Q, N, idx, v);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) v[a] = __ldg(p + (27 + a) * N);
             const float sp = sum9(v);
             if (side < 0) Th = 2.0f * d.T_H - Th;
             if (side > 0) Th = 2.0f * d.T_C - Th;
@@ -324,8 +405,48 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2)
             s_phs[ey - 1][ex - 1] = ps - (d.rhoA + ph * d.drho) * kCs2;
         }
     }
+
+    if (use_tma) {
+        const bool ok = mbar_wait_bounded(bar, 0);
+        if (__syncthreads_or(!ok)) {
+            // the copy did not complete in time: report it, and keep the block
+            // resident for one more bounded wait so that no transfer into its
+            // shared memory can outlive it
+            if (tid == 0) {
+                atomicExch(err, 1);
+                mbar_wait_bounded(bar, 0);
+            }
+            return;
+        }
+    }
+
+    // ---- own-node moments ----------------------------------------------------------
+    float phi, T, psi, pst, jx, jy;
+    {
+        float v[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = s_pop[a][ty][tx];
+        phi = sum9(v);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = s_pop[9 + a][ty][tx];
+        pst = sum9(v);
+        jx = mx9(v);
+        jy = my9(v);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = s_pop[18 + a][ty][tx];
+        T = sum9(v);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = s_pop[27 + a][ty][tx];
+        psi = sum9(v);
+        float Tg = T;
+        if (own_side < 0) Tg = 2.0f * d.T_H - T;
+        if (own_side > 0) Tg = 2.0f * d.T_C - T;
+        s_phi[ty + 2][tx + 2] = phi;
+        s_sig[ty + 1][tx + 1] = sigma_eos(d, Tg, psi);
+        s_phs[ty + 1][tx + 1] = pst - (d.rhoA + phi * d.drho) * kCs2;
+    }
     __syncthreads();
-    // ---- unit normals n = grad phi / |grad phi| on tile + 1-node halo -----------
+    // ---- unit normals on tile + 1-node halo ---------------------------------------------
     for (int i = tid; i < RW * RH; i += TX * TY) {
         const int cx = i % RW, cy = i / RW;
         float gxp, gyp;
@@ -337,7 +458,7 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2)
     __syncthreads();
     if (!active) return;
 
-    // ---- stencils, forces, velocity, pressure (Sec. 3, App. C) --------------------
+    // ---- stencils, forces, velocity, pressure (Sec. 3, App. C) --------------------------
     const int r = ty + 1, c = tx + 1;
     float gpx, gpy;
     grad_smem<EW>(s_phi, ty + 2, tx + 2, gpx, gpy);
@@ -359,14 +480,13 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2)
     const float Fty = deltas * (-sig * kappa * n_y + sgy - n_y * ndots) + d.Fext_y -
                       (rho - d.rhoA) * d.gravity;
     const float Fpx = -phx, Fpy = -phy;
-    const float jx = mx9(g), jy = my9(g);
     const float ux = (3.0f * jx + 0.5f * Ftx) * inv_rho;
     const float uy = (3.0f * jy + 0.5f * Fty) * inv_rho;
     const float Gam = Fpx * ux + Fpy * uy;
     const float p = pst + 0.5f * Gam;
 
     if (kMode == kFields) {
-        const size_t o = (size_t)gy * d.nx + gx;
+        const int o = gy * d.nx + gx;
         dst[o] = phi;
         dst[N + o] = ux;
         dst[2 * N + o] = uy;
@@ -376,34 +496,45 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2)
         return;
     }
 
+    const Nbr nb = neighbours(d, gx, gy);
+    const int wall = !d.walls ? 0 : (gy == 1 ? -1 : (gy == d.ny - 2 ? 1 : 0));
+    float v[9];
     // ---- f: conservative Allen-Cahn (App. B) ---------------------------------------
     {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = s_pop[a][ty][tx];
         const float theta_m = d.mphi_4_over_W * phi * (1.0f - phi);   // M_phi theta
-        scalar_collide(f, phi, theta_m * n_x, theta_m * n_y, d.omega_phi, ux, uy);
-        push_store<false>(d, dst, N, gx, gy, f);
+        scalar_collide(v, phi, theta_m * n_x, theta_m * n_y, d.omega_phi, ux, uy);
+        store_set<false>(dst, N, nb, v, wall, 0.0f);
     }
     // ---- h: energy (App. D), rate from the local thermal diffusivity -----------------
     {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = s_pop[18 + a][ty][tx];
         const float alpha = d.alphaA + phi * d.dalpha;
         const float wT = 1.0f / (3.0f * alpha + 0.5f);
-        scalar_collide(h, T, 0.0f, 0.0f, wT, ux, uy);
-        push_store<true>(d, dst + 18 * N, N, gx, gy, h);
+        scalar_collide(v, T, 0.0f, 0.0f, wT, ux, uy);
+        store_set<true>(dst + 18 * (size_t)N, N, nb, v, wall, wall < 0 ? d.T_H : d.T_C);
     }
     // ---- q: surfactant (App. E) -------------------------------------------------
     {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = s_pop[27 + a][ty][tx];
         const float dG = (phi - 0.5f) * (d.g_s32 * phi * (1.0f - phi) + d.g_w);
         const float flux = -d.m_psi * psi * (1.0f - psi) * dG;   // times grad phi
-        scalar_collide(q, psi, flux * gpx, flux * gpy, d.omega_psi, ux, uy);
-        push_store<false>(d, dst + 27 * N, N, gx, gy, q);
+        scalar_collide(v, psi, flux * gpx, flux * gpy, d.omega_psi, ux, uy);
+        store_set<false>(dst + 27 * (size_t)N, N, nb, v, wall, 0.0f);
     }
     // ---- g: two-fluid pressure/velocity (App. C) ----------------------------------------
     {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = s_pop[9 + a][ty][tx];
         const float mu = d.muA + phi * d.dmu;
         const float wn = 1.0f / (3.0f * mu * inv_rho + 0.5f);
         const float vp = p - rho * kCs2;                      // varphi = p - rho c_s^2
         const float ux2 = ux * ux, uy2 = uy * uy;
-        float c[9];
-        pop_to_central(g, ux, uy, c);
+        float cm[9];
+        pop_to_central(v, ux, uy, cm);
         // equilibria (Eq. (31)) and sources (Eq. (32))
         const float e20 = p * kCs2 + vp * ux2, e02 = p * kCs2 + vp * uy2;
         const float e11 = vp * ux * uy;
@@ -426,17 +557,17 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2)
         dc[0] = Gam;
         dc[1] = s10;
         dc[2] = s01;
-        const float d2s = (e20 + e02) + 0.5f * (s20 + s02) - (c[3] + c[4]);
-        const float k2d = c[3] - c[4];
+        const float d2s = (e20 + e02) + 0.5f * (s20 + s02) - (cm[3] + cm[4]);
+        const float k2d = cm[3] - cm[4];
         const float d2d = wn * ((e20 - e02) - k2d) + (1.0f - 0.5f * wn) * (s20 - s02);
         dc[3] = 0.5f * (d2s + d2d);
         dc[4] = 0.5f * (d2s - d2d);
-        dc[5] = wn * (e11 - c[5]) + (1.0f - 0.5f * wn) * s11;
-        dc[6] = e21 - c[6];
-        dc[7] = e12 - c[7];
-        dc[8] = e22 - c[8];
-        add_central_increment(g, dc, ux, uy);
-        push_store<false>(d, dst + 9 * N, N, gx, gy, g);
+        dc[5] = wn * (e11 - cm[5]) + (1.0f - 0.5f * wn) * s11;
+        dc[6] = e21 - cm[6];
+        dc[7] = e12 - cm[7];
+        dc[8] = e22 - cm[8];
+        add_central_increment(v, dc, ux, uy);
+        store_set<false>(dst + 9 * (size_t)N, N, nb, v, wall, 0.0f);
     }
 }
 
@@ -592,15 +723,26 @@ dim3 step_grid(const LbmDev& d)
 
 }  // namespace
 
-cudaError_t launch_step(const LbmDev& d, const float* src, float* dst, cudaStream_t s)
+cudaError_t launch_step(const LbmDev& d, const float* src, float* dst, const CUtensorMap* tmap,
+                        int* err, cudaStream_t s)
 {
-    step_kernel<kStep><<<step_grid(d), dim3(kTileX, kTileY), 0, s>>>(d, src, dst);
+    if (tmap)
+        step_kernel<kStep, true><<<step_grid(d), dim3(kTileX, kTileY), 0, s>>>(d, src, dst, *tmap, err);
+    else
+        step_kernel<kStep, false><<<step_grid(d), dim3(kTileX, kTileY), 0, s>>>(d, src, dst,
+                                                                                CUtensorMap{}, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fields(const LbmDev& d, const float* src, float* fields, cudaStream_t s)
+cudaError_t launch_fields(const LbmDev& d, const float* src, float* fields, const CUtensorMap* tmap,
+                          int* err, cudaStream_t s)
 {
-    step_kernel<kFields><<<step_grid(d), dim3(kTileX, kTileY), 0, s>>>(d, src, fields);
+    if (tmap)
+        step_kernel<kFields, true><<<step_grid(d), dim3(kTileX, kTileY), 0, s>>>(d, src, fields,
+                                                                                 *tmap, err);
+    else
+        step_kernel<kFields, false><<<step_grid(d), dim3(kTileX, kTileY), 0, s>>>(
+            d, src, fields, CUtensorMap{}, err);
     return cudaGetLastError();
 }
 
