@@ -4,9 +4,10 @@ Default workload: the 256x1024 channel sweep -- nine simulations, Gibbs
 elasticity beta in {0.05, 0.1, 0.2} x quadratic sensitivity sigma_TT in
 {5e-4, 1e-3, 2e-3}, bubble R=32 a quarter of the way along the channel,
 density ratio 10, FP32 storage.  One benchmark step advances every
-simulation of the batch by one time step (nine launches of the fused step
-kernel, interleaved, so each simulation's 75 MB state has been evicted from
-the 129 MB L2 by the other eight before it is read again).
+simulation of the batch by one time step: by default one launch of the
+batched step kernel over all nine (--mode plain: nine launches, one per
+simulation).  Each simulation's 75 MB state has been evicted from the 129 MB
+L2 by the other eight before it is read again.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -222,29 +223,35 @@ def run_gpu(args) -> None:
     for s in sims:
         s.init()                      # analytic initial state, built on the device
     torch.cuda.synchronize()
-    for _ in range(args.warmup):
-        for s in sims:
-            s.step(1)
-    torch.cuda.synchronize()
-    launches0 = sum(s.launches() for s in sims)
 
     def barrier():
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    with ClockSampler(dev_index) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            for s in sims:
+    def step_all():
+        if args.mode == "batched":
+            lbm.lbm_step_batch(sims, 1)       # one launch over every simulation
+        else:
+            for s in sims:                   # one launch per simulation
                 s.step(1)
+
+    def timed(nsteps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        l0 = sum(s.launches() for s in sims)
+        ev0.record(stream)
+        for _ in range(nsteps):
+            step_all()
         ev1.record(stream)
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    launches = sum(s.launches() for s in sims) - launches0
+        return ev0.elapsed_time(ev1), sum(s.launches() for s in sims) - l0
+
+    for _ in range(args.warmup):
+        step_all()
+    with ClockSampler(dev_index) as clk:
+        ms, launches = timed(args.steps)
     clocks = clk.summary()
 
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
@@ -255,12 +262,23 @@ def run_gpu(args) -> None:
     value = total_nodes / (ms_max * 1e-3) / 1e6
 
     # roofline of the dominant kernel: every launch in the timed region is the
-    # fused step kernel
+    # fused step kernel (one simulation, or the whole batch, per launch)
     per_launch_ms = ms / launches
-    per_launch_bytes = BYTES_PER_NODE_STEP * nodes_per_step / len(params)
+    sims_per_launch = len(params) if args.mode == "batched" else 1
+    per_launch_bytes = BYTES_PER_NODE_STEP * nodes_per_step / len(params) * sims_per_launch
     peaks = measured_peaks()
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
     traffic = profiled_traffic(args.workload)
+
+    # the other launch mode on the same simulations, for comparison
+    other = None
+    if args.compare_modes and len(params) > 1:
+        mode = args.mode
+        args.mode = "plain" if mode == "batched" else "batched"
+        ms_o, _ = timed(max(args.steps // 4, 1))
+        other = {"mode": args.mode,
+                 "value": nodes_per_step * max(args.steps // 4, 1) / (ms_o * 1e-3) / 1e6}
+        args.mode = mode
 
     e2e = run_e2e(args, lbm, torch, stream, params) if not args.no_e2e else None
 
@@ -277,6 +295,7 @@ def run_gpu(args) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "lattices": [f"{p['nx']}x{p['ny']}" for p in params],
                        "sims_per_gpu": len(params), "fluid_nodes_per_step": nodes_per_step,
+                       "launch_mode": args.mode, "other_mode": other,
                        "l2": "working set %.0f MB > 129 MB L2; simulations interleaved per step"
                              % (len(params) * 2 * 144 * params[0]["nx"] * params[0]["ny"] / 1e6),
                        "parallelism": f"replicas x{ws}"},
@@ -313,8 +332,11 @@ def run_e2e(args, lbm, torch, stream, params) -> dict:
     while done < steps:
         n = min(100, steps - done)
         for _ in range(n):             # interleaved, as in the device-timed loop
-            for s in sims:
-                s.step(1)
+            if args.mode == "batched":
+                lbm.lbm_step_batch(sims, 1)
+            else:
+                for s in sims:
+                    s.step(1)
         for s in sims:
             s.observe()
             d2h += 8 * 8
@@ -340,6 +362,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="channel_256x1024_sweep",
                     choices=["channel_256x1024_sweep", "channel_1024x4096", "channel_64x128"])
+    ap.add_argument("--mode", default="batched", choices=["batched", "plain"],
+                    help="batched: one launch per step over all simulations; "
+                         "plain: one launch per simulation")
+    ap.add_argument("--compare-modes", action="store_true", default=True)
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -151,6 +151,16 @@ lbm_status lbm_init(lbm_sim* sim, const double* fields, const float* populations
  * LBM_ECUDA. */
 lbm_status lbm_step(lbm_sim* sim, int64_t nsteps);
 
+/* Advances n simulations (1 <= n <= 48) by nsteps time steps with one kernel
+ * launch per step covering the tiles of all of them; the simulations may
+ * differ in size and parameters.  Each step is the same fused update as
+ * lbm_step, so the result of every simulation equals what lbm_step gives it
+ * alone.  All sims must be initialised, distinct, and created on the same
+ * device and stream; the launches are issued on that stream (asynchronous)
+ * and counted by lbm_launch_count of sims[0].  Errors: LBM_EINVAL,
+ * LBM_ESTATE, LBM_ECUDA. */
+lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps);
+
 /* Computes the observables of the current state (out may be NULL) and, if
  * host_fields != NULL, copies the macroscopic fields phi, u_x, u_y, p, T, psi
  * into the host double array [6][ny][nx] (wall rows set to 0).  Synchronises

@@ -7,6 +7,6 @@ ABI of ``include/lbm.h``; :mod:`.lbm` is its Python binding.
 """
 from .lbm import (  # noqa: F401
     LbmError, Sim, load, lbm_create, lbm_derive, lbm_create_ex, lbm_destroy, lbm_get_derived,
-    lbm_get_populations, lbm_init, lbm_launch_count, lbm_observe, lbm_step,
+    lbm_get_populations, lbm_init, lbm_launch_count, lbm_observe, lbm_step, lbm_step_batch,
     lbm_workspace_bytes,
 )

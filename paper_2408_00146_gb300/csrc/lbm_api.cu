@@ -442,6 +442,49 @@ lbm_status lbm_step(lbm_sim* s, int64_t nsteps)
     return LBM_OK;
 }
 
+lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
+{
+    if (!sims || n < 1 || n > kMaxBatch)
+        return fail(LBM_EINVAL, "lbm_step_batch needs 1..%d sims (got %d)", kMaxBatch, n);
+    if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+    long long total = 0;
+    for (int i = 0; i < n; ++i) {
+        const lbm_sim* s = sims[i];
+        if (!s) return fail(LBM_EINVAL, "sim %d is NULL", i);
+        if (!s->ready) return fail(LBM_ESTATE, "sim %d not initialised", i);
+        if (s->stream != sims[0]->stream || s->device != sims[0]->device)
+            return fail(LBM_EINVAL, "sim %d is on another stream or device than sim 0", i);
+        for (int j = 0; j < i; ++j)
+            if (sims[j] == s) return fail(LBM_EINVAL, "sim %d appears twice", i);
+        total += tiles_of(s->dev);
+    }
+    if (total > 0x7fffffffLL) return fail(LBM_EINVAL, "too many tiles in one batch");
+    static thread_local BatchArgs args;  // 14 KB: kept off the stack
+    args.n = n;
+    args.first[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        args.dev[i] = sims[i]->dev;
+        args.err[i] = sims[i]->err;
+        args.first[i + 1] = args.first[i] + tiles_of(sims[i]->dev);
+    }
+    for (int64_t k = 0; k < nsteps; ++k) {
+        for (int i = 0; i < n; ++i) {
+            lbm_sim* s = sims[i];
+            args.src[i] = s->pop[s->cur];
+            args.dst[i] = s->pop[s->cur ^ 1];
+            args.has_tmap[i] = s->have_tmap ? 1 : 0;
+            if (s->have_tmap) args.tmap[i] = s->tmap[s->cur];
+        }
+        CUDA_TRY(launch_step_batch(args, (int)total, sims[0]->stream));
+        sims[0]->launches += 1;
+        for (int i = 0; i < n; ++i) {
+            sims[i]->cur ^= 1;
+            sims[i]->t += 1;
+        }
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_observe(lbm_sim* s, lbm_obs* out, double* host_fields)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");

@@ -45,6 +45,23 @@ cudaError_t launch_step(const LbmDev& d, const float* src, float* dst, const CUt
                         int* err, cudaStream_t s);
 cudaError_t launch_fields(const LbmDev& d, const float* src, float* fields, const CUtensorMap* tmap,
                           int* err, cudaStream_t s);
+// One launch stepping up to kMaxBatch simulations (lbm_step_batch): the grid
+// is the concatenation of every simulation's tiles; first[] holds the prefix
+// sums of the tile counts.  Passed by value as a kernel parameter.
+constexpr int kMaxBatch = 48;
+struct BatchArgs {
+    CUtensorMap tmap[kMaxBatch];  // 64-byte aligned descriptors (first member)
+    LbmDev dev[kMaxBatch];
+    const float* src[kMaxBatch];
+    float* dst[kMaxBatch];
+    int* err[kMaxBatch];
+    int first[kMaxBatch + 1];
+    int has_tmap[kMaxBatch];
+    int n;
+};
+cudaError_t launch_step_batch(const BatchArgs& args, int total_tiles, cudaStream_t s);
+int tiles_of(const LbmDev& d);
+
 cudaError_t launch_analytic_fields(const LbmDev& d, float* fields, cudaStream_t s);
 cudaError_t launch_init_equilibrium(const LbmDev& d, const float* fields, float* pops,
                                     cudaStream_t s);

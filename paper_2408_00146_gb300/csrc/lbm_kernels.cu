@@ -330,9 +330,9 @@ __device__ __forceinline__ int wrap_x(const LbmDev& d, int x)
 // valid), else by per-thread loads that also resolve periodic images and
 // wall mirrors for the slots past the lattice edge.
 template <int kMode, bool kTma>
-__global__ void __launch_bounds__(kTileX * kTileY, 3)
-    step_kernel(LbmDev d, const float* __restrict__ src, float* __restrict__ dst,
-                const __grid_constant__ CUtensorMap tmap, int* __restrict__ err)
+__device__ __forceinline__ void step_tile(const LbmDev& d, const float* __restrict__ src,
+                                          float* __restrict__ dst, const CUtensorMap* tmap,
+                                          int* __restrict__ err, int bx, int by)
 {
     constexpr int TX = kTileX, TY = kTileY;
     constexpr int EW = TX + 4, EH = TY + 4;   // phi tile with a 2-node halo
@@ -347,15 +347,15 @@ __global__ void __launch_bounds__(kTileX * kTileY, 3)
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
-    const int x0 = blockIdx.x * TX;
-    const int fy0 = blockIdx.y * TY;          // tile origin in fluid-row numbering
+    const int x0 = bx * TX;
+    const int fy0 = by * TY;                  // tile origin in fluid-row numbering
     const int N = d.nx * d.ny;
 
     const int gx = x0 + tx;
     const int gfy = fy0 + ty;
     const bool active = (gx < d.nx) && (gfy < d.nfy);
     const int gy = d.y0 + gfy;
-    const bool use_tma = kTma && (x0 + TX <= d.nx) && (fy0 + TY <= d.nfy);
+    const bool use_tma = kTma && tmap != nullptr && (x0 + TX <= d.nx) && (fy0 + TY <= d.nfy);
     const uint32_t bar = smem_addr(&s_bar);
 
     // ---- own-node populations into shared memory ------------------------------------
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kTileX * kTileY, 3)
         __syncthreads();
         if (tid == 0) {
             mbar_expect_tx(bar, 36u * TX * TY * sizeof(float));
-            tma_load_tile(smem_addr(&s_pop[0][0][0]), &tmap, x0, d.y0 + fy0, bar);
+            tma_load_tile(smem_addr(&s_pop[0][0][0]), tmap, x0, d.y0 + fy0, bar);
         }
     } else {
         const int sx = wrap_x(d, gx);
@@ -571,6 +571,30 @@ __global__ void __launch_bounds__(kTileX * kTileY, 3)
     }
 }
 
+template <int kMode, bool kTma>
+__global__ void __launch_bounds__(kTileX * kTileY, 3)
+    step_kernel(LbmDev d, const float* __restrict__ src, float* __restrict__ dst,
+                const __grid_constant__ CUtensorMap tmap, int* __restrict__ err)
+{
+    step_tile<kMode, kTma>(d, src, dst, &tmap, err, blockIdx.x, blockIdx.y);
+}
+
+// Many simulations in one launch: block b takes tile b - first[s] of the
+// simulation s with first[s] <= b < first[s + 1], tiles numbered row by row.
+template <bool kTma>
+__global__ void __launch_bounds__(kTileX * kTileY, 3)
+    step_batch_kernel(const __grid_constant__ BatchArgs args)
+{
+    const int b = blockIdx.x;
+    int s = 0;
+    while (s + 1 < args.n && b >= args.first[s + 1]) ++s;
+    const int t = b - args.first[s];
+    const int tiles_x = (args.dev[s].nx + kTileX - 1) / kTileX;
+    step_tile<kStep, kTma>(args.dev[s], args.src[s], args.dst[s],
+                           args.has_tmap[s] ? &args.tmap[s] : nullptr, args.err[s],
+                           t % tiles_x, t / tiles_x);
+}
+
 // Equilibrium populations of every fluid node from the macroscopic fields
 // (initial state): P^-1 F(-u) applied to the equilibria of Eqs. (26), (31),
 // (37), (42), with n and R from the isotropic stencil of phi.
@@ -743,6 +767,17 @@ cudaError_t launch_fields(const LbmDev& d, const float* src, float* fields, cons
     else
         step_kernel<kFields, false><<<step_grid(d), dim3(kTileX, kTileY), 0, s>>>(
             d, src, fields, CUtensorMap{}, err);
+    return cudaGetLastError();
+}
+
+int tiles_of(const LbmDev& d)
+{
+    return ((d.nx + kTileX - 1) / kTileX) * ((d.nfy + kTileY - 1) / kTileY);
+}
+
+cudaError_t launch_step_batch(const BatchArgs& args, int total_tiles, cudaStream_t s)
+{
+    step_batch_kernel<true><<<total_tiles, dim3(kTileX, kTileY), 0, s>>>(args);
     return cudaGetLastError();
 }
 

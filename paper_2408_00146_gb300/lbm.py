@@ -51,6 +51,7 @@ STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA"
 # Symbols include/lbm.h declares.
 EXPORTS = [
     "lbm_derive", "lbm_workspace_bytes", "lbm_create", "lbm_create_ex", "lbm_init", "lbm_step",
+    "lbm_step_batch",
     "lbm_observe", "lbm_get_populations", "lbm_get_derived", "lbm_launch_count",
     "lbm_destroy", "lbm_last_error", "lbm_reduce_observables_noalloc",
 ]
@@ -93,6 +94,7 @@ def load() -> ctypes.CDLL:
             L.lbm_create_ex.argtypes = [PP, vp, vp, sz, ctypes.POINTER(vp)]
             L.lbm_init.argtypes = [vp, dp, fp]
             L.lbm_step.argtypes = [vp, ctypes.c_int64]
+            L.lbm_step_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_int64]
             L.lbm_observe.argtypes = [vp, ctypes.POINTER(LbmObs), dp]
             L.lbm_get_populations.argtypes = [vp, fp]
             L.lbm_get_derived.argtypes = [vp, dp]
@@ -177,6 +179,14 @@ def lbm_init(sim, fields: np.ndarray | None = None, populations: np.ndarray | No
 
 def lbm_step(sim, nsteps: int):
     _check(load().lbm_step(sim, int(nsteps)), "lbm_step")
+
+
+def lbm_step_batch(sims, nsteps: int):
+    """One launch per step over every simulation in `sims` (handles or Sim)."""
+    hs = [s.handle if isinstance(s, Sim) else s for s in sims]
+    arr = (ctypes.c_void_p * len(hs))(*[h.value if isinstance(h, ctypes.c_void_p) else h
+                                        for h in hs])
+    _check(load().lbm_step_batch(arr, len(hs), int(nsteps)), "lbm_step_batch")
 
 
 def lbm_observe(sim, host_fields: np.ndarray | None = None, check: bool = True) -> dict:
