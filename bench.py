@@ -45,6 +45,11 @@ def workload(name: str) -> list[dict]:
         return [si.channel_1024x4096()]
     if name == "channel_64x128":
         return [si.channel_64x128()]
+    if name == "channel_512x1024":
+        # profiling case: one lattice with 150 MB of populations (> L2)
+        p = si.channel_256x1024()
+        p.update(nx=512, xb=256.0)
+        return [p]
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -361,7 +366,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="channel_256x1024_sweep",
-                    choices=["channel_256x1024_sweep", "channel_1024x4096", "channel_64x128"])
+                    choices=["channel_256x1024_sweep", "channel_1024x4096", "channel_64x128",
+                             "channel_512x1024"])
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"],
                     help="batched: one launch per step over all simulations; "
                          "plain: one launch per simulation")
