@@ -134,6 +134,24 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def max_over_ranks(ms: float, device: str) -> float:
+    """Maximum of a per-rank time over all ranks (identity without a process
+    group).  The only collective of the benchmark: the simulations are
+    independent, nothing on the data path is exchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(ms_max: float, nodes_per_step: int, steps: int, world: int) -> float:
+    """Whole-job MLUPS: every rank advanced its own copy of the batch."""
+    return nodes_per_step * steps * world / (ms_max * 1e-3) / 1e6
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -259,12 +277,8 @@ def run_gpu(args) -> None:
         ms, launches = timed(args.steps)
     clocks = clk.summary()
 
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    total_nodes = nodes_per_step * args.steps * ws
-    value = total_nodes / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, "cuda")
+    value = weak_scaling_value(ms_max, nodes_per_step, args.steps, ws)
 
     # roofline of the dominant kernel: every launch in the timed region is the
     # fused step kernel (one simulation, or the whole batch, per launch)
