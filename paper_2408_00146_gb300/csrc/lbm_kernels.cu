@@ -572,7 +572,7 @@ __device__ __forceinline__ void step_tile(const LbmDev& d, const float* __restri
 }
 
 template <int kMode, bool kTma>
-__global__ void __launch_bounds__(kTileX * kTileY, 3)
+__global__ void __launch_bounds__(kTileX * kTileY, 4)
     step_kernel(LbmDev d, const float* __restrict__ src, float* __restrict__ dst,
                 const __grid_constant__ CUtensorMap tmap, int* __restrict__ err)
 {
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(kTileX * kTileY, 3)
 // Many simulations in one launch: block b takes tile b - first[s] of the
 // simulation s with first[s] <= b < first[s + 1], tiles numbered row by row.
 template <bool kTma>
-__global__ void __launch_bounds__(kTileX * kTileY, 3)
+__global__ void __launch_bounds__(kTileX * kTileY, 4)
     step_batch_kernel(const __grid_constant__ BatchArgs args)
 {
     const int b = blockIdx.x;
