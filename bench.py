@@ -33,7 +33,12 @@ import numpy as np  # noqa: E402
 
 import seeded_inputs as si  # noqa: E402
 
-BYTES_PER_NODE_STEP = 288          # read + write of 4 x 9 FP32 populations
+# algorithmic bytes per fluid node and step: read + write of the node's
+# state -- 36 FP32 populations; or, with 16-bit storage, 36 16-bit deviations
+# and the float4 of rest-state moments
+BYTES_PER_NODE_STEP = {"fp32": 288, "fp16": 176, "bf16": 176}
+BYTES_PER_NODE_BUFFER = {"fp32": 144, "fp16": 88, "bf16": 88}
+PRECISION_CODE = {"fp32": 0, "fp16": 1, "bf16": 2}
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
 KERNEL_SRC = os.path.join(ROOT, "paper_2408_00146_gb300", "csrc", "lbm_kernels.cu")
 
@@ -71,14 +76,20 @@ def kernel_hash() -> str:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def profiled_traffic(work: str):
+def step_kernel_name(mode: str, precision: str) -> str:
+    if precision == "fp32":
+        return "step_batch_kernel" if mode == "batched" else "step_kernel"
+    return "step_batch_dev_kernel" if mode == "batched" else "step_dev_kernel"
+
+
+def profiled_traffic(work: str, mode: str, precision: str):
     """DRAM bytes per step-kernel launch from the committed ncu summary, if it
-    was taken on the current kernel source for this workload."""
+    was taken on the current kernel source for this workload and launch."""
     if not os.path.exists(PROFILE_TRAFFIC):
         return None
     with open(PROFILE_TRAFFIC) as fh:
         d = json.load(fh)
-    ent = d.get(work)
+    ent = d.get(f"{work}/{precision}/{step_kernel_name(mode, precision)}")
     if not ent or ent.get("kernel_sha256_16") != kernel_hash():
         return None
     return float(ent["dram_bytes_per_launch"])
@@ -240,6 +251,8 @@ def run_gpu(args) -> None:
     dev_index = torch.cuda.current_device()
     stream = torch.cuda.Stream()
     params = workload(args.workload)
+    for p in params:
+        p["precision"] = PRECISION_CODE[args.precision]
     nodes_per_step = sum(fluid_nodes(p) for p in params)
 
     sims = [lbm.Sim(p, stream=stream, workspace="torch") for p in params]
@@ -284,10 +297,12 @@ def run_gpu(args) -> None:
     # fused step kernel (one simulation, or the whole batch, per launch)
     per_launch_ms = ms / launches
     sims_per_launch = len(params) if args.mode == "batched" else 1
-    per_launch_bytes = BYTES_PER_NODE_STEP * nodes_per_step / len(params) * sims_per_launch
+    bpn = BYTES_PER_NODE_STEP[args.precision]
+    per_launch_bytes = bpn * nodes_per_step / len(params) * sims_per_launch
     peaks = measured_peaks()
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-    traffic = profiled_traffic(args.workload)
+    kernel = step_kernel_name(args.mode, args.precision)
+    traffic = profiled_traffic(args.workload, args.mode, args.precision)
 
     # the other launch mode on the same simulations, for comparison
     other = None
@@ -315,13 +330,15 @@ def run_gpu(args) -> None:
             "config": {"workload": args.workload, "lattices": [f"{p['nx']}x{p['ny']}" for p in params],
                        "sims_per_gpu": len(params), "fluid_nodes_per_step": nodes_per_step,
                        "launch_mode": args.mode, "other_mode": other,
+                       "storage": args.precision,
                        "l2": "working set %.0f MB > 129 MB L2; simulations interleaved per step"
-                             % (len(params) * 2 * 144 * params[0]["nx"] * params[0]["ny"] / 1e6),
+                             % (sum(2 * BYTES_PER_NODE_BUFFER[args.precision] * p["nx"] * p["ny"]
+                                    for p in params) / 1e6),
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                          "traffic": traffic, "peak_source": peaks["source"],
-                         "kernel": "step_kernel", "bytes_per_node_step": BYTES_PER_NODE_STEP},
+                         "kernel": kernel, "bytes_per_node_step": bpn},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -338,7 +355,7 @@ def run_e2e(args, lbm, torch, stream, params) -> dict:
     from the host, steps, the observables read back every 100 steps and the
     final fields copied to the host, all inside the timed region."""
     steps = max(args.e2e_steps, 1)
-    host_in = [si.bubble_fields(p) for p in params]
+    host_in = [si.bubble_fields(p) for p in params]   # params carry the precision
     host_out = [np.empty((6, p["ny"], p["nx"])) for p in params]
     sims = [lbm.Sim(p, stream=stream, workspace="torch") for p in params]
     torch.cuda.synchronize()
@@ -385,6 +402,8 @@ def main():
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"],
                     help="batched: one launch per step over all simulations; "
                          "plain: one launch per simulation")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="population storage (arithmetic is FP32 in every case)")
     ap.add_argument("--compare-modes", action="store_true", default=True)
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--no-e2e", action="store_true")

@@ -49,7 +49,21 @@ typedef enum {
     LBM_ESTATE = -6     /* call out of order (e.g. lbm_step before init)    */
 } lbm_status;
 
-enum { LBM_FP32 = 0 }; /* population storage precision (lbm_params.precision) */
+/* Population storage precision (lbm_params.precision).  The arithmetic is
+ * FP32 in every mode; the paper fixes no storage format (its method is stated
+ * in exact arithmetic).
+ *   LBM_FP32: the 36 populations of each node in FP32 (144 B per node and
+ *     buffer).
+ *   LBM_FP16, LBM_BF16: per node, the FP32 zeroth moments M = (M_f, M_g, M_h,
+ *     M_q) of the populations it pushed at the last step (16 B), and per
+ *     population its deviation from w_a M of the node that pushed it (the
+ *     source y - e_a, or the node itself for a population that bounced back),
+ *     stored in IEEE binary16 or bfloat16 (72 B per node and buffer).  The
+ *     rest part carries the conserved scalars phi, T, psi in FP32; the
+ *     rounding errors of the nine deviations a node pushes are folded into its
+ *     M, so the populations it pushes sum to their FP32 values.  Populations
+ *     at the API (lbm_init, lbm_get_populations) stay FP32 arrays. */
+enum { LBM_FP32 = 0, LBM_FP16 = 1, LBM_BF16 = 2 };
 
 /* Problem parameters, named as in the paper's problem statement (Sec. 2,
  * Sec. 6).  Lattice units throughout.  The lattice parameters derived from
@@ -79,7 +93,7 @@ typedef struct {
     double gravity;        /* buoyancy -(rho - rho_A) g along y (Sec. 5.3)      */
     double nu_A;           /* > 0: ambient kinematic viscosity given directly   */
     double alpha_A;        /* > 0: ambient thermal diffusivity given directly   */
-    int32_t precision;     /* LBM_FP32                                          */
+    int32_t precision;     /* LBM_FP32, LBM_FP16 or LBM_BF16 (storage, above)   */
 } lbm_params;
 
 /* Observables (Sec. 5.3, Sec. 6): phi-weighted bubble centroid ("mass
@@ -106,8 +120,9 @@ typedef struct {
  * without creating a sim (host only; no CUDA call).  Errors: LBM_EINVAL. */
 lbm_status lbm_derive(const lbm_params* p, double* out);
 
-/* Bytes of device workspace one sim needs (two population buffers of
- * 36 floats per node, one field buffer of 6 floats per node, reduction
+/* Bytes of device workspace one sim needs (two population buffers -- 36
+ * floats per node for LBM_FP32; 36 16-bit deviations and 4 floats per node for
+ * LBM_FP16/LBM_BF16 -- one field buffer of 6 floats per node, reduction
  * scratch).  Errors: LBM_EINVAL for invalid parameters. */
 lbm_status lbm_workspace_bytes(const lbm_params* p, size_t* bytes);
 
@@ -131,7 +146,9 @@ lbm_status lbm_create_ex(const lbm_params* p, void* stream, void* workspace,
  *   populations != NULL: host float array [4][9][ny][nx] (sets f, g, h, q;
  *     directions in the order e_0..e_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),
  *     (1,1),(-1,1),(-1,-1),(1,-1); wall rows are ignored), copied as the
- *     post-streaming populations of t = 0;
+ *     post-streaming populations of t = 0 (16-bit storage: each node's M is
+ *     set to the sums of its own nine populations, and the deviations are
+ *     rounded from the given values);
  *   else fields != NULL: host double array [6][ny][nx] of phi, u_x, u_y, p,
  *     T, psi; every population is set to the equilibrium of App. B-E built
  *     from these fields (n and R from the isotropic stencils of phi);
@@ -152,8 +169,9 @@ lbm_status lbm_init(lbm_sim* sim, const double* fields, const float* populations
 lbm_status lbm_step(lbm_sim* sim, int64_t nsteps);
 
 /* Advances n simulations (1 <= n <= 48) by nsteps time steps with one kernel
- * launch per step covering the tiles of all of them; the simulations may
- * differ in size and parameters.  Each step is the same fused update as
+ * launch per step and storage precision covering the tiles of all the sims
+ * of that precision; the simulations may differ in size, parameters and
+ * precision.  Each step is the same fused update as
  * lbm_step, so the result of every simulation equals what lbm_step gives it
  * alone.  All sims must be initialised, distinct, and created on the same
  * device and stream; the launches are issued on that stream (asynchronous)
@@ -169,8 +187,10 @@ lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps);
 lbm_status lbm_observe(lbm_sim* sim, lbm_obs* out, double* host_fields);
 
 /* Copies the current post-streaming populations into the host float array
- * [4][9][ny][nx] (the layout lbm_init accepts back: checkpoint/restart).
- * Synchronises the stream.  Errors: LBM_ESTATE, LBM_ECUDA. */
+ * [4][9][ny][nx] (the layout lbm_init accepts back: checkpoint/restart; wall
+ * rows hold 0).  16-bit storage: the populations are rebuilt as
+ * w_a M(source) + deviation in FP32.  Synchronises the stream.  Errors:
+ * LBM_ESTATE, LBM_ECUDA. */
 lbm_status lbm_get_populations(lbm_sim* sim, float* host_pops);
 
 /* Writes the LBM_NDERIVED lattice parameters listed above.  Errors:

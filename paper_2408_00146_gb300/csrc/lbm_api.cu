@@ -50,7 +50,8 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 lbm_status derive(const lbm_params* p, double* out)
 {
     if (!p) return fail(LBM_EINVAL, "params is NULL");
-    if (p->precision != LBM_FP32) return fail(LBM_EINVAL, "precision %d unsupported", p->precision);
+    if (p->precision != LBM_FP32 && p->precision != LBM_FP16 && p->precision != LBM_BF16)
+        return fail(LBM_EINVAL, "precision %d unsupported", p->precision);
     if (p->walls != 0 && p->walls != 1) return fail(LBM_EINVAL, "walls must be 0 or 1");
     if (p->nx < 4 || p->ny < (p->walls ? 5 : 4))
         return fail(LBM_EINVAL, "lattice %dx%d too small", p->nx, p->ny);
@@ -148,15 +149,24 @@ LbmDev make_dev(const lbm_params* p, const double* dv)
     return d;
 }
 
+// Workspace: two population buffers, the fields, the reduction scratch.  A
+// population buffer is 36 FP32 planes, or (16-bit storage) 36 16-bit planes
+// followed, at dev_bytes, by one float4 of rest-state moments per node.
 struct Layout {
-    size_t pop_bytes, fld_bytes, part_bytes, res_bytes, total;
+    size_t pop_bytes, dev_bytes, fld_bytes, part_bytes, res_bytes, total;
 };
 
 Layout layout_of(const lbm_params* p)
 {
     Layout L;
     const size_t N = (size_t)p->nx * p->ny;
-    L.pop_bytes = align256(36 * N * sizeof(float));
+    if (p->precision == LBM_FP32) {
+        L.dev_bytes = 0;
+        L.pop_bytes = align256(36 * N * sizeof(float));
+    } else {
+        L.dev_bytes = align256(36 * N * 2);
+        L.pop_bytes = L.dev_bytes + align256(N * 4 * sizeof(float));
+    }
     L.fld_bytes = align256(6 * N * sizeof(float));
     L.part_bytes = align256((size_t)kReduceBlocks * 8 * sizeof(double));
     L.res_bytes = align256(16 * sizeof(double));
@@ -182,7 +192,8 @@ struct lbm_sim {
     bool owns_ws;
     void* ws;
     size_t ws_bytes;
-    float* pop[2];
+    void* pop[2];    // FP32 populations, or 16-bit deviations
+    float4* mom[2];  // 16-bit storage: rest-state moments (else NULL)
     float* fld;
     double* part;
     double* res;
@@ -274,14 +285,20 @@ static lbm_status create_impl(const lbm_params* p, void* stream, void* ws, size_
     s->ws = ws;
     s->ws_bytes = ws_bytes;
     char* base = static_cast<char*>(ws);
-    s->pop[0] = reinterpret_cast<float*>(base);
-    s->pop[1] = reinterpret_cast<float*>(base + L.pop_bytes);
+    s->pop[0] = base;
+    s->pop[1] = base + L.pop_bytes;
+    s->mom[0] = s->mom[1] = nullptr;
+    if (p->precision != LBM_FP32) {
+        s->mom[0] = reinterpret_cast<float4*>(base + L.dev_bytes);
+        s->mom[1] = reinterpret_cast<float4*>(base + L.pop_bytes + L.dev_bytes);
+    }
     s->fld = reinterpret_cast<float*>(base + 2 * L.pop_bytes);
     s->part = reinterpret_cast<double*>(base + 2 * L.pop_bytes + L.fld_bytes);
     s->res = reinterpret_cast<double*>(base + 2 * L.pop_bytes + L.fld_bytes + L.part_bytes);
     s->err = reinterpret_cast<int*>(s->res + 12);
-    s->have_tmap = encode_population_maps(s);
-    e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+    s->have_tmap = p->precision == LBM_FP32 && encode_population_maps(s);
+    e = p->precision == LBM_FP32 ? cudaSuccess : prepare_dev_storage(p->precision);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s->h_res), 16 * sizeof(double));
     if (e != cudaSuccess) {
         lbm_destroy(s);
@@ -353,24 +370,90 @@ static lbm_status ensure_stage(lbm_sim* s)
     return LBM_OK;
 }
 
+// One step from buffer `from` to the other one, on stream st.
+static cudaError_t step_once(lbm_sim* s, int from, cudaStream_t st)
+{
+    if (s->p.precision == LBM_FP32)
+        return launch_step(s->dev, static_cast<const float*>(s->pop[from]),
+                           static_cast<float*>(s->pop[from ^ 1]), map_of(s, from), s->err, st);
+    return launch_step_dev(s->dev, s->p.precision, s->pop[from], s->mom[from], s->pop[from ^ 1],
+                           s->mom[from ^ 1], nullptr, st);
+}
+
+// The fields [6][ny][nx] of the state in buffer `buf`, into s->fld.
+static cudaError_t fields_of(lbm_sim* s, int buf)
+{
+    if (s->p.precision == LBM_FP32)
+        return launch_fields(s->dev, static_cast<const float*>(s->pop[buf]), s->fld,
+                             map_of(s, buf), s->err, s->stream);
+    return launch_step_dev(s->dev, s->p.precision, s->pop[buf], s->mom[buf], nullptr, nullptr,
+                           s->fld, s->stream);
+}
+
+static size_t pop_buffer_bytes(const lbm_sim* s)
+{
+    const size_t N = (size_t)s->p.nx * s->p.ny;
+    return s->p.precision == LBM_FP32 ? 36 * N * sizeof(float) : layout_of(&s->p).pop_bytes;
+}
+
+// 16-bit storage from host FP32 populations: M of every node = the sums of its
+// own nine populations per set (FP64, rounded once), then the deviations,
+// six planes at a time through the field buffer, their rounding errors
+// gathered in the other buffer's M and folded into M.
+static lbm_status split_host_populations(lbm_sim* s, const float* populations)
+{
+    const int nx = s->p.nx, ny = s->p.ny;
+    const size_t N = (size_t)nx * ny;
+    lbm_status st = ensure_stage(s);
+    if (st != LBM_OK) return st;
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    for (size_t o = 0; o < N; ++o)
+        for (int set = 0; set < 4; ++set) {
+            double acc = 0.0;
+            for (int a = 0; a < 9; ++a) acc += populations[(size_t)(9 * set + a) * N + o];
+            s->h_stage[4 * o + set] = (float)acc;
+        }
+    CUDA_TRY(cudaMemcpyAsync(s->mom[0], s->h_stage, 4 * N * sizeof(float), cudaMemcpyHostToDevice,
+                             s->stream));
+    for (int a0 = 0; a0 < 36; a0 += 6) {
+        CUDA_TRY(cudaStreamSynchronize(s->stream));  // staging buffer free
+        std::memcpy(s->h_stage, populations + (size_t)a0 * N, 6 * N * sizeof(float));
+        CUDA_TRY(cudaMemcpyAsync(s->fld, s->h_stage, 6 * N * sizeof(float),
+                                 cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(launch_split_planes(s->dev, s->p.precision, s->fld, a0, 6, s->mom[0], s->pop[0],
+                                     s->mom[1], s->stream));
+        s->launches += 1;
+    }
+    CUDA_TRY(launch_fold_lost(s->dev, s->mom[0], s->mom[1], s->stream));
+    s->launches += 1;
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
 lbm_status lbm_init(lbm_sim* s, const double* fields, const float* populations)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     const size_t N = (size_t)s->p.nx * s->p.ny;
+    const bool fp32 = s->p.precision == LBM_FP32;
     s->ready = false;
     s->cur = 0;
     s->t = 0;
-    if (populations) {
-        CUDA_TRY(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    if (populations && fp32) {
         CUDA_TRY(cudaMemcpyAsync(s->pop[0], populations, 36 * N * sizeof(float),
                                  cudaMemcpyHostToDevice, s->stream));
         CUDA_TRY(cudaStreamSynchronize(s->stream));
         s->ready = true;
         return LBM_OK;
     }
-    CUDA_TRY(cudaMemsetAsync(s->pop[0], 0, 36 * N * sizeof(float), s->stream));
-    CUDA_TRY(cudaMemsetAsync(s->pop[1], 0, 36 * N * sizeof(float), s->stream));
-    CUDA_TRY(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->pop[0], 0, pop_buffer_bytes(s), s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->pop[1], 0, pop_buffer_bytes(s), s->stream));
+    if (populations) {
+        lbm_status st = split_host_populations(s, populations);
+        if (st != LBM_OK) return st;
+        s->ready = true;
+        return LBM_OK;
+    }
     if (fields) {
         lbm_status st = ensure_stage(s);
         if (st != LBM_OK) return st;
@@ -382,7 +465,11 @@ lbm_status lbm_init(lbm_sim* s, const double* fields, const float* populations)
         CUDA_TRY(launch_analytic_fields(s->dev, s->fld, s->stream));
         s->launches += 1;
     }
-    CUDA_TRY(launch_init_equilibrium(s->dev, s->fld, s->pop[0], s->stream));
+    if (fp32)
+        CUDA_TRY(launch_init_equilibrium(s->dev, s->fld, static_cast<float*>(s->pop[0]),
+                                         s->stream));
+    else
+        CUDA_TRY(launch_init_dev(s->dev, s->p.precision, s->fld, s->pop[0], s->mom[0], s->stream));
     s->launches += 1;
     if (fields) CUDA_TRY(cudaStreamSynchronize(s->stream));
     s->ready = true;
@@ -395,8 +482,7 @@ static lbm_status build_graph(lbm_sim* s)
     // whose inputs are the workspace buffers.
     CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kGraphSteps; ++i) {
-        cudaError_t e = launch_step(s->dev, s->pop[i & 1], s->pop[(i + 1) & 1], map_of(s, i & 1),
-                                    s->err, s->cap_stream);
+        cudaError_t e = step_once(s, i & 1, s->cap_stream);
         if (e != cudaSuccess) {
             cudaGraph_t g;
             cudaStreamEndCapture(s->cap_stream, &g);
@@ -421,7 +507,7 @@ lbm_status lbm_step(lbm_sim* s, int64_t nsteps)
             if (st != LBM_OK) return st;
         }
         if (s->cur == 1) {
-            CUDA_TRY(launch_step(s->dev, s->pop[1], s->pop[0], map_of(s, 1), s->err, s->stream));
+            CUDA_TRY(step_once(s, 1, s->stream));
             s->cur = 0;
             --left;
             s->launches += 1;
@@ -433,8 +519,7 @@ lbm_status lbm_step(lbm_sim* s, int64_t nsteps)
         }
     }
     for (; left > 0; --left) {
-        CUDA_TRY(launch_step(s->dev, s->pop[s->cur], s->pop[s->cur ^ 1], map_of(s, s->cur), s->err,
-                             s->stream));
+        CUDA_TRY(step_once(s, s->cur, s->stream));
         s->cur ^= 1;
         s->launches += 1;
     }
@@ -459,24 +544,44 @@ lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
         total += tiles_of(s->dev);
     }
     if (total > 0x7fffffffLL) return fail(LBM_EINVAL, "too many tiles in one batch");
-    static thread_local BatchArgs args;  // 14 KB: kept off the stack
-    args.n = n;
-    args.first[0] = 0;
-    for (int i = 0; i < n; ++i) {
-        args.dev[i] = sims[i]->dev;
-        args.err[i] = sims[i]->err;
-        args.first[i + 1] = args.first[i] + tiles_of(sims[i]->dev);
+    // one launch per storage precision present, each over the tiles of the
+    // sims of that precision
+    static thread_local BatchArgs args[3];  // 15 KB each: kept off the stack
+    int tiles[3] = {0, 0, 0};
+    lbm_sim* group[3][kMaxBatch];
+    for (int k = 0; k < 3; ++k) {
+        args[k].n = 0;
+        args[k].first[0] = 0;
     }
-    for (int64_t k = 0; k < nsteps; ++k) {
-        for (int i = 0; i < n; ++i) {
-            lbm_sim* s = sims[i];
-            args.src[i] = s->pop[s->cur];
-            args.dst[i] = s->pop[s->cur ^ 1];
-            args.has_tmap[i] = s->have_tmap ? 1 : 0;
-            if (s->have_tmap) args.tmap[i] = s->tmap[s->cur];
+    for (int i = 0; i < n; ++i) {
+        const int k = sims[i]->p.precision;
+        BatchArgs& a = args[k];
+        group[k][a.n] = sims[i];
+        a.dev[a.n] = sims[i]->dev;
+        a.err[a.n] = sims[i]->err;
+        a.first[a.n + 1] = a.first[a.n] + tiles_of(sims[i]->dev);
+        tiles[k] = a.first[a.n + 1];
+        a.n += 1;
+    }
+    for (int64_t step = 0; step < nsteps; ++step) {
+        for (int k = 0; k < 3; ++k) {
+            BatchArgs& a = args[k];
+            if (a.n == 0) continue;
+            for (int i = 0; i < a.n; ++i) {
+                lbm_sim* s = group[k][i];
+                a.src[i] = s->pop[s->cur];
+                a.dst[i] = s->pop[s->cur ^ 1];
+                a.msrc[i] = s->mom[s->cur];
+                a.mdst[i] = s->mom[s->cur ^ 1];
+                a.has_tmap[i] = s->have_tmap ? 1 : 0;
+                if (s->have_tmap) a.tmap[i] = s->tmap[s->cur];
+            }
+            if (k == LBM_FP32)
+                CUDA_TRY(launch_step_batch(a, tiles[k], sims[0]->stream));
+            else
+                CUDA_TRY(launch_step_batch_dev(a, k, tiles[k], sims[0]->stream));
+            sims[0]->launches += 1;
         }
-        CUDA_TRY(launch_step_batch(args, (int)total, sims[0]->stream));
-        sims[0]->launches += 1;
         for (int i = 0; i < n; ++i) {
             sims[i]->cur ^= 1;
             sims[i]->t += 1;
@@ -490,7 +595,7 @@ lbm_status lbm_observe(lbm_sim* s, lbm_obs* out, double* host_fields)
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     if (!s->ready) return fail(LBM_ESTATE, "lbm_observe before lbm_init");
     const size_t N = (size_t)s->p.nx * s->p.ny;
-    CUDA_TRY(launch_fields(s->dev, s->pop[s->cur], s->fld, map_of(s, s->cur), s->err, s->stream));
+    CUDA_TRY(fields_of(s, s->cur));
     CUDA_TRY(launch_observe_reduce(s->dev, s->fld, s->part, kReduceBlocks, s->res, s->stream));
     s->launches += 3;
     CUDA_TRY(cudaMemcpyAsync(s->h_res, s->res, 13 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -541,8 +646,20 @@ lbm_status lbm_get_populations(lbm_sim* s, float* host_pops)
     if (!s || !host_pops) return fail(LBM_EINVAL, "NULL argument");
     if (!s->ready) return fail(LBM_ESTATE, "lbm_get_populations before lbm_init");
     const size_t N = (size_t)s->p.nx * s->p.ny;
-    CUDA_TRY(cudaMemcpyAsync(host_pops, s->pop[s->cur], 36 * N * sizeof(float),
-                             cudaMemcpyDeviceToHost, s->stream));
+    if (s->p.precision == LBM_FP32) {
+        CUDA_TRY(cudaMemcpyAsync(host_pops, s->pop[s->cur], 36 * N * sizeof(float),
+                                 cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        return LBM_OK;
+    }
+    // rebuilt six planes at a time through the field buffer
+    for (int a0 = 0; a0 < 36; a0 += 6) {
+        CUDA_TRY(launch_join_planes(s->dev, s->p.precision, s->pop[s->cur], s->mom[s->cur], a0, 6,
+                                    s->fld, s->stream));
+        s->launches += 1;
+        CUDA_TRY(cudaMemcpyAsync(host_pops + (size_t)a0 * N, s->fld, 6 * N * sizeof(float),
+                                 cudaMemcpyDeviceToHost, s->stream));
+    }
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     return LBM_OK;
 }

@@ -52,8 +52,10 @@ constexpr int kMaxBatch = 48;
 struct BatchArgs {
     CUtensorMap tmap[kMaxBatch];  // 64-byte aligned descriptors (first member)
     LbmDev dev[kMaxBatch];
-    const float* src[kMaxBatch];
-    float* dst[kMaxBatch];
+    const void* src[kMaxBatch];   // populations (FP32) or deviations (16-bit)
+    void* dst[kMaxBatch];
+    const void* msrc[kMaxBatch];  // rest-state moments (float4 per node), 16-bit storage only
+    void* mdst[kMaxBatch];
     int* err[kMaxBatch];
     int first[kMaxBatch + 1];
     int has_tmap[kMaxBatch];
@@ -61,6 +63,31 @@ struct BatchArgs {
 };
 cudaError_t launch_step_batch(const BatchArgs& args, int total_tiles, cudaStream_t s);
 int tiles_of(const LbmDev& d);
+
+// 16-bit population storage (precision LBM_FP16 / LBM_BF16): deviations
+// dev[36][ny][nx] from the rest states mom[ny][nx] (float4: f, g, h, q).
+// prepare_dev_storage: per-device kernel attributes, before the first launch.
+cudaError_t prepare_dev_storage(int precision);
+// One step dsrc/msrc -> ddst/mdst, or, with fields != NULL, the fields of the
+// state dsrc/msrc ([6][ny][nx], as launch_fields).
+cudaError_t launch_step_dev(const LbmDev& d, int precision, const void* dsrc, const float4* msrc,
+                            void* ddst, float4* mdst, float* fields, cudaStream_t s);
+// Batched step of sims that all have this precision (src/dst/msrc/mdst used).
+cudaError_t launch_step_batch_dev(const BatchArgs& args, int precision, int total_tiles,
+                                  cudaStream_t s);
+// Initial state from the fields (as launch_init_equilibrium).
+cudaError_t launch_init_dev(const LbmDev& d, int precision, const float* fields, void* dev,
+                            float4* mom, cudaStream_t s);
+// FP32 population planes a0 .. a0+count-1 (planes[count][ny][nx]) to
+// deviations from mom, and back (join writes 0 on wall rows).  split sums
+// the deviations' rounding errors per node and set into lost (a float4 per
+// node, cleared when a0 == 0); launch_fold_lost then adds them to mom.
+cudaError_t launch_split_planes(const LbmDev& d, int precision, const float* planes, int a0,
+                                int count, const float4* mom, void* dev, float4* lost,
+                                cudaStream_t s);
+cudaError_t launch_fold_lost(const LbmDev& d, float4* mom, const float4* lost, cudaStream_t s);
+cudaError_t launch_join_planes(const LbmDev& d, int precision, const void* dev, const float4* mom,
+                               int a0, int count, float* planes, cudaStream_t s);
 
 cudaError_t launch_analytic_fields(const LbmDev& d, float* fields, cudaStream_t s);
 cudaError_t launch_init_equilibrium(const LbmDev& d, const float* fields, float* pops,

@@ -45,6 +45,9 @@ DERIVED_NAMES = [
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = (
     0, -1, -2, -3, -4, -5, -6)
+# Population storage precision (lbm_params.precision).
+LBM_FP32, LBM_FP16, LBM_BF16 = 0, 1, 2
+PRECISIONS = {"fp32": LBM_FP32, "fp16": LBM_FP16, "bf16": LBM_BF16}
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
                 -4: "LBM_EUNSTABLE", -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE"}
 

@@ -75,3 +75,11 @@ def test_workspace_bytes_layout():
     # two population buffers (36 floats/node) + fields (6 floats/node) + scratch
     assert ws >= (2 * 36 + 6) * 4 * n
     assert ws < (2 * 36 + 6) * 4 * n + 64 * 1024
+    # 16-bit storage: per buffer 36 two-byte deviations + a float4 of rest
+    # moments per node
+    for prec in (lbm.LBM_FP16, lbm.LBM_BF16):
+        q = dict(p, precision=prec)
+        ws16 = lbm.lbm_workspace_bytes(q)
+        assert ws16 >= (2 * (36 * 2 + 16) + 6 * 4) * n
+        assert ws16 < (2 * (36 * 2 + 16) + 6 * 4) * n + 64 * 1024
+        assert lbm.lbm_derive(q)["U_o"] == lbm.lbm_derive(p)["U_o"]
