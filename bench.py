@@ -50,6 +50,9 @@ def workload(name: str) -> list[dict]:
         return [si.channel_1024x4096()]
     if name == "channel_64x128":
         return [si.channel_64x128()]
+    if name == "ensemble_64":
+        # 64 channels of uneven size (nx 128..512, ny = 4 nx) and physics
+        return si.ensemble_channels(64, seed=0)
     if name == "channel_512x1024":
         # profiling case: one lattice with 150 MB of populations (> L2)
         p = si.channel_256x1024()
@@ -315,6 +318,7 @@ def run_gpu(args) -> None:
         args.mode = mode
 
     e2e = run_e2e(args, lbm, torch, stream, params) if not args.no_e2e else None
+    served = run_served(args, torch) if (args.serve_requests > 0 and rank == 0) else None
 
     for s in sims:
         s.close()
@@ -341,6 +345,7 @@ def run_gpu(args) -> None:
                          "kernel": kernel, "bytes_per_node_step": bpn},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "served": served,
             "gpu_launches": launches,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                        "reasons": clocks["reasons"]},
@@ -348,6 +353,31 @@ def run_gpu(args) -> None:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_served(args, torch) -> dict:
+    """The served workload: a Poisson stream of requests (uneven lattices,
+    physics and storage precisions) through the serving loop, arrivals in
+    wall time; p50/p99 of arrival-to-finish latency and aggregate MLUPS."""
+    from paper_2408_00146_gb300.serve import LbmEngine, Server, requests_from_stream, summary
+
+    stream = si.request_stream(n=args.serve_requests, rate=args.serve_rate, seed=0)
+    reqs = requests_from_stream(stream, max_steps=args.serve_max_steps, tol=1e-6)
+    free, _total = torch.cuda.mem_get_info()
+    budget = int(min(150e9, 0.8 * free))
+    srv = Server(LbmEngine(), budget_bytes=budget, round_steps=100)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    out = summary(res, wall, srv.node_steps)
+    out.update({"rate_per_s": args.serve_rate, "max_steps": args.serve_max_steps,
+                "tol": 1e-6, "round_steps": 100, "budget_gb": budget / 1e9,
+                "peak_resident": srv.peak_resident, "peak_gb": srv.peak_bytes / 1e9,
+                "fp16_requests": sum(p["precision"] == 1 for _, p in stream),
+                "lattices": "nx log-uniform 64..512 (x16), ny = 4 nx"})
+    return out
 
 
 def run_e2e(args, lbm, torch, stream, params) -> dict:
@@ -398,7 +428,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="channel_256x1024_sweep",
                     choices=["channel_256x1024_sweep", "channel_1024x4096", "channel_64x128",
-                             "channel_512x1024"])
+                             "channel_512x1024", "ensemble_64"])
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"],
                     help="batched: one launch per step over all simulations; "
                          "plain: one launch per simulation")
@@ -408,6 +438,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests of the served workload (0: skip it)")
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-max-steps", type=int, default=3000)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -168,7 +168,7 @@ lbm_status lbm_init(lbm_sim* sim, const double* fields, const float* populations
  * LBM_ECUDA. */
 lbm_status lbm_step(lbm_sim* sim, int64_t nsteps);
 
-/* Advances n simulations (1 <= n <= 48) by nsteps time steps with one kernel
+/* Advances n simulations (1 <= n <= 64) by nsteps time steps with one kernel
  * launch per step and storage precision covering the tiles of all the sims
  * of that precision; the simulations may differ in size, parameters and
  * precision.  Each step is the same fused update as

@@ -546,7 +546,7 @@ lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
     if (total > 0x7fffffffLL) return fail(LBM_EINVAL, "too many tiles in one batch");
     // one launch per storage precision present, each over the tiles of the
     // sims of that precision
-    static thread_local BatchArgs args[3];  // 15 KB each: kept off the stack
+    static thread_local BatchArgs args[3];  // 20 KB each: kept off the stack
     int tiles[3] = {0, 0, 0};
     lbm_sim* group[3][kMaxBatch];
     for (int k = 0; k < 3; ++k) {

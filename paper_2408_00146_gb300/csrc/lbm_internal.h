@@ -48,7 +48,7 @@ cudaError_t launch_fields(const LbmDev& d, const float* src, float* fields, cons
 // One launch stepping up to kMaxBatch simulations (lbm_step_batch): the grid
 // is the concatenation of every simulation's tiles; first[] holds the prefix
 // sums of the tile counts.  Passed by value as a kernel parameter.
-constexpr int kMaxBatch = 48;
+constexpr int kMaxBatch = 64;
 struct BatchArgs {
     CUtensorMap tmap[kMaxBatch];  // 64-byte aligned descriptors (first member)
     LbmDev dev[kMaxBatch];

@@ -1,0 +1,202 @@
+"""Serving of many independent bubble-migration simulations on one GPU.
+
+Requests (one parameter set each, arriving over time) are admitted while
+their device workspaces fit a memory budget, kept resident, and advanced
+together: every round steps all resident simulations by ``round_steps``
+time steps with ``lbm_step_batch`` (one kernel launch per step and storage
+precision for up to 64 simulations), then reads each one's observables.  A
+simulation finishes when its bubble velocity |U| (the phi-weighted mean
+velocity of Sec. 6) falls below ``tol`` after having exceeded 100 tol (the
+bubble starts at rest) or it reaches its step cap; its
+memory is released and waiting requests are admitted before the next round
+(continuous batching).  Each simulation's trajectory is independent of what
+else is resident, because a batched step computes every simulation exactly
+as a step of its own would.
+
+The scheduler only orders work on the host; every step of every simulation
+runs in the CUDA kernels behind the C ABI.  ``Server`` takes an engine
+object so that its policy can be exercised without a GPU.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+from collections import deque
+
+MAX_BATCH = 64   # simulations per lbm_step_batch call (the C ABI's limit)
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    params: dict
+    arrival: float = 0.0           # seconds after the start of the run
+    max_steps: int = 300_000
+    tol: float = 1e-6
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    steps: int
+    converged: bool
+    status: str                    # "converged", "step cap" or an error
+    obs: dict
+    nodes: int
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class LbmEngine:
+    """Engine over the C ABI: workspaces from PyTorch's caching allocator
+    (no cudaMalloc per request), all simulations on one stream."""
+
+    def __init__(self, stream=None):
+        import torch
+
+        from . import lbm
+        self.lbm = lbm
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+
+    def workspace_bytes(self, params: dict) -> int:
+        return self.lbm.lbm_workspace_bytes(params)
+
+    def open(self, params: dict):
+        sim = self.lbm.Sim(params, stream=self.stream, workspace="torch")
+        sim.init()                  # analytic initial state, built on the device
+        return sim
+
+    def step(self, sims: list, n: int) -> None:
+        for i in range(0, len(sims), MAX_BATCH):
+            self.lbm.lbm_step_batch(sims[i:i + MAX_BATCH], n)
+
+    def observe(self, sim) -> dict:
+        return sim.observe(check=False)
+
+    def close(self, sim) -> None:
+        sim.close()
+
+
+def fluid_nodes(p: dict) -> int:
+    return int(p["nx"]) * (int(p["ny"]) - 2 if p.get("walls", 1) else int(p["ny"]))
+
+
+class Server:
+    """Admission by memory budget, resident state, continuous batching.
+
+    clock: returns seconds; wait(dt): lets dt seconds pass when nothing is
+    resident and the next request has not arrived yet.  Defaults are wall
+    time; tests pass a virtual clock."""
+
+    def __init__(self, engine, budget_bytes: int, round_steps: int = 100,
+                 clock=time.perf_counter, wait=time.sleep):
+        if round_steps < 1:
+            raise ValueError("round_steps must be >= 1")
+        self.engine = engine
+        self.budget = int(budget_bytes)
+        self.round_steps = int(round_steps)
+        self.clock = clock
+        self.wait = wait
+        self.node_steps = 0
+        self.rounds = 0
+        self.peak_bytes = 0
+        self.peak_resident = 0
+
+    def run(self, requests: list[Request]) -> list[Result]:
+        for r in requests:
+            if self.engine.workspace_bytes(r.params) > self.budget:
+                raise ValueError(f"request {r.rid} needs more memory than the whole budget")
+        pending = deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
+        waiting: list[Request] = []
+        resident: dict[int, dict] = {}        # rid -> {req, sim, bytes, steps, admitted}
+        used = 0
+        results: list[Result] = []
+        t0 = self.clock()
+
+        def now() -> float:
+            return self.clock() - t0
+
+        while pending or waiting or resident:
+            t = now()
+            while pending and pending[0].arrival <= t:
+                waiting.append(pending.popleft())
+            # admission: first fit in arrival order
+            still = []
+            for r in waiting:
+                nbytes = self.engine.workspace_bytes(r.params)
+                if used + nbytes <= self.budget:
+                    used += nbytes
+                    resident[r.rid] = dict(req=r, sim=self.engine.open(r.params), bytes=nbytes,
+                                           steps=0, admitted=now(), moving=False)
+                else:
+                    still.append(r)
+            waiting = still
+            self.peak_bytes = max(self.peak_bytes, used)
+            self.peak_resident = max(self.peak_resident, len(resident))
+            if not resident:
+                if pending:
+                    self.wait(max(pending[0].arrival - now(), 0.0))
+                continue
+            # one round: every resident simulation advances round_steps steps
+            order = sorted(resident)
+            self.engine.step([resident[k]["sim"] for k in order], self.round_steps)
+            self.rounds += 1
+            for k in order:
+                ent = resident[k]
+                ent["steps"] += self.round_steps
+                self.node_steps += fluid_nodes(ent["req"].params) * self.round_steps
+                ob = self.engine.observe(ent["sim"])
+                u = math.hypot(ob["ux_bub"], ob["uy_bub"])
+                status = None
+                ent["moving"] = ent["moving"] or u >= 100.0 * ent["req"].tol
+                if ob.get("status", 0) != 0 or not math.isfinite(u):
+                    status = f"error {ob.get('status', 0)}"
+                elif ent["moving"] and u < ent["req"].tol:
+                    status = "converged"
+                elif ent["steps"] >= ent["req"].max_steps:
+                    status = "step cap"
+                if status is None:
+                    continue
+                self.engine.close(ent["sim"])
+                used -= ent["bytes"]
+                r = ent["req"]
+                results.append(Result(rid=r.rid, arrival=r.arrival, admitted=ent["admitted"],
+                                      finished=now(), steps=ent["steps"],
+                                      converged=status == "converged", status=status,
+                                      obs=dict(ob), nodes=fluid_nodes(r.params)))
+                del resident[k]
+        return sorted(results, key=lambda r: r.rid)
+
+
+def percentile(values: list[float], q: float) -> float:
+    """q-th percentile (0..100) by linear interpolation between order
+    statistics."""
+    if not values:
+        return float("nan")
+    v = sorted(values)
+    pos = (len(v) - 1) * q / 100.0
+    lo = int(math.floor(pos))
+    hi = min(lo + 1, len(v) - 1)
+    return v[lo] + (v[hi] - v[lo]) * (pos - lo)
+
+
+def summary(results: list[Result], wall_s: float, node_steps: int) -> dict:
+    lat = [r.latency for r in results]
+    return {"requests": len(results),
+            "converged": sum(r.converged for r in results),
+            "p50_latency_s": percentile(lat, 50.0), "p99_latency_s": percentile(lat, 99.0),
+            "mlups": node_steps / wall_s / 1e6 if wall_s > 0 else float("nan"),
+            "wall_s": wall_s}
+
+
+def requests_from_stream(stream: list[tuple[float, dict]], max_steps: int,
+                         tol: float = 1e-6) -> list[Request]:
+    return [Request(rid=i, params=p, arrival=t, max_steps=max_steps, tol=tol)
+            for i, (t, p) in enumerate(stream)]

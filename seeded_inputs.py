@@ -149,3 +149,49 @@ def parity_fields(p: dict, seed: int = 0) -> np.ndarray:
     the step (velocity-dependent transforms, forces, stencils) is non-zero."""
     return bubble_fields(p, seed=seed, psi_noise=1e-3, u_noise=1e-3, T_noise=1e-3,
                          p_noise=1e-5)
+
+
+# ---- ensembles and request streams ------------------------------------------------
+
+def ensemble_channels(n: int = 64, seed: int = 0, nx_range=(128, 512)) -> list[dict]:
+    """n independent channels of uneven size and physics: nx uniform over the
+    multiples of 32 in nx_range, ny = 4 nx, bubble R = nx/8 a quarter of the
+    way along the channel; Gibbs elasticity beta ~ U(0, 0.3), quadratic
+    sensitivity sigma_TT log-uniform in [2e-4, 4e-3], Marangoni number
+    Ma ~ U(5, 50); the rest as the 64x128 channel."""
+    rng = np.random.default_rng(seed)
+    sizes = np.arange(nx_range[0], nx_range[1] + 1, 32)
+    out = []
+    for _ in range(n):
+        nx = int(rng.choice(sizes))
+        p = channel_64x128()
+        p.update(nx=nx, ny=4 * nx, R=nx / 8.0, xb=nx / 2.0, yb=float(nx),
+                 beta=float(rng.uniform(0.0, 0.3)),
+                 sigma_TT=float(np.exp(rng.uniform(np.log(2e-4), np.log(4e-3)))),
+                 Ma=float(rng.uniform(5.0, 50.0)))
+        out.append(p)
+    return out
+
+
+def request_stream(n: int = 500, rate: float = 20.0, seed: int = 0, nx_range=(64, 512),
+                   fp16_share: float = 0.5) -> list[tuple[float, dict]]:
+    """Poisson request arrivals (exponential gaps of mean 1/rate seconds) of
+    channels with nx log-uniform in nx_range rounded to a multiple of 16,
+    ny = 4 nx, the physics distributions of ensemble_channels, and 16-bit
+    population storage with probability fp16_share.  Returns (arrival
+    time in seconds, parameters) pairs in arrival order."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        nx = int(round(np.exp(rng.uniform(np.log(nx_range[0]), np.log(nx_range[1]))) / 16.0)) * 16
+        nx = max(nx, 16)
+        p = channel_64x128()
+        p.update(nx=nx, ny=4 * nx, R=nx / 8.0, xb=nx / 2.0, yb=float(nx),
+                 beta=float(rng.uniform(0.0, 0.3)),
+                 sigma_TT=float(np.exp(rng.uniform(np.log(2e-4), np.log(4e-3)))),
+                 Ma=float(rng.uniform(5.0, 50.0)),
+                 precision=1 if rng.uniform() < fp16_share else 0)
+        out.append((t, p))
+    return out
