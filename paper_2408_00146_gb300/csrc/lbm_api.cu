@@ -208,6 +208,10 @@ struct lbm_sim {
     int* err;        // device flag: a bounded wait in a kernel gave up
     bool have_tmap;  // TMA descriptors of both population buffers are valid
     CUtensorMap tmap[2];
+    bool ystream;    // steps use the y-streaming kernel (stream_eligible, TMA side maps)
+    CUtensorMap tside[2];
+    int strip_chunks;  // chunks per strip when stepped alone
+    int num_sms;
 };
 
 namespace {
@@ -236,10 +240,16 @@ bool encode_population_maps(lbm_sim* s)
                                    (cuuint64_t)s->p.nx * s->p.ny * sizeof(float)};
     const cuuint32_t box[3] = {(cuuint32_t)kTileX, (cuuint32_t)kTileY, 36};
     const cuuint32_t estride[3] = {1, 1, 1};
+    const cuuint32_t side_box[3] = {4, (cuuint32_t)kTileY, 36};
     for (int b = 0; b < 2; ++b) {
         CUresult r = encode(&s->tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->pop[b], dims, strides,
                             box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+        // side boxes of the streaming kernel: four columns on either side
+        r = encode(&s->tside[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->pop[b], dims, strides,
+                   side_box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return false;
     }
     return true;
@@ -297,7 +307,15 @@ static lbm_status create_impl(const lbm_params* p, void* stream, void* ws, size_
     s->res = reinterpret_cast<double*>(base + 2 * L.pop_bytes + L.fld_bytes + L.part_bytes);
     s->err = reinterpret_cast<int*>(s->res + 12);
     s->have_tmap = p->precision == LBM_FP32 && encode_population_maps(s);
+    s->ystream = s->have_tmap && stream_eligible(s->dev);
     e = p->precision == LBM_FP32 ? cudaSuccess : prepare_dev_storage(p->precision);
+    if (e == cudaSuccess && s->ystream) {
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+        if (e == cudaSuccess) e = prepare_stream();
+        s->num_sms = sms > 0 ? sms : 1;
+        s->strip_chunks = stream_strip_chunks(s->dev, stream_columns(s->dev), s->num_sms);
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s->h_res), 16 * sizeof(double));
     if (e != cudaSuccess) {
@@ -370,9 +388,28 @@ static lbm_status ensure_stage(lbm_sim* s)
     return LBM_OK;
 }
 
+// Entry i of a streaming launch: sim s stepping from buffer `from`.
+static void stream_entry(StreamBatchArgs& a, int i, const lbm_sim* s, int from, int strip_chunks)
+{
+    a.tmap[i] = s->tmap[from];
+    a.tside[i] = s->tside[from];
+    a.dev[i] = s->dev;
+    a.dst[i] = s->pop[from ^ 1];
+    a.err[i] = s->err;
+    a.strip_chunks[i] = strip_chunks;
+    a.first[i + 1] = a.first[i] + stream_blocks(s->dev, strip_chunks);
+}
+
 // One step from buffer `from` to the other one, on stream st.
 static cudaError_t step_once(lbm_sim* s, int from, cudaStream_t st)
 {
+    if (s->ystream) {
+        static thread_local StreamBatchArgs a;   // 26 KB: kept off the stack
+        a.n = 1;
+        a.first[0] = 0;
+        stream_entry(a, 0, s, from, s->strip_chunks);
+        return launch_stream_batch(a, st);
+    }
     if (s->p.precision == LBM_FP32)
         return launch_step(s->dev, static_cast<const float*>(s->pop[from]),
                            static_cast<float*>(s->pop[from ^ 1]), map_of(s, from), s->err, st);
@@ -544,16 +581,24 @@ lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
         total += tiles_of(s->dev);
     }
     if (total > 0x7fffffffLL) return fail(LBM_EINVAL, "too many tiles in one batch");
-    // one launch per storage precision present, each over the tiles of the
-    // sims of that precision
+    // one launch per kernel family present: the streaming kernel for the
+    // FP32 sims it takes, the tile kernel per storage precision for the rest
     static thread_local BatchArgs args[3];  // 20 KB each: kept off the stack
+    static thread_local StreamBatchArgs sargs;
     int tiles[3] = {0, 0, 0};
     lbm_sim* group[3][kMaxBatch];
+    lbm_sim* sgroup[kMaxBatch];
+    int sn = 0, scols = 0;
     for (int k = 0; k < 3; ++k) {
         args[k].n = 0;
         args[k].first[0] = 0;
     }
     for (int i = 0; i < n; ++i) {
+        if (sims[i]->ystream) {
+            sgroup[sn++] = sims[i];
+            scols += stream_columns(sims[i]->dev);
+            continue;
+        }
         const int k = sims[i]->p.precision;
         BatchArgs& a = args[k];
         group[k][a.n] = sims[i];
@@ -563,7 +608,17 @@ lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
         tiles[k] = a.first[a.n + 1];
         a.n += 1;
     }
+    int schunks[kMaxBatch];
+    for (int i = 0; i < sn; ++i)
+        schunks[i] = stream_strip_chunks(sgroup[i]->dev, scols, sgroup[i]->num_sms);
     for (int64_t step = 0; step < nsteps; ++step) {
+        if (sn > 0) {
+            sargs.n = sn;
+            sargs.first[0] = 0;
+            for (int i = 0; i < sn; ++i) stream_entry(sargs, i, sgroup[i], sgroup[i]->cur, schunks[i]);
+            CUDA_TRY(launch_stream_batch(sargs, sims[0]->stream));
+            sims[0]->launches += 1;
+        }
         for (int k = 0; k < 3; ++k) {
             BatchArgs& a = args[k];
             if (a.n == 0) continue;

@@ -89,6 +89,30 @@ cudaError_t launch_fold_lost(const LbmDev& d, float4* mom, const float4* lost, c
 cudaError_t launch_join_planes(const LbmDev& d, int precision, const void* dev, const float4* mom,
                                int a0, int count, float* planes, cudaStream_t s);
 
+// Streaming step (FP32 storage, walls, nx a multiple of kTileX) of up to
+// kMaxBatch simulations per launch: blocks walk kTileX-wide columns in +y
+// over strips of strip_chunks[s] 8-row chunks, reading the populations
+// through tmap[s] (box {kTileX, kTileY, 36}) and tside[s] (box {4, kTileY,
+// 36}), TMA descriptors of the source buffer; first[] holds the prefix sums
+// of stream_blocks.  prepare_stream: per-device kernel attribute.
+struct StreamBatchArgs {
+    CUtensorMap tmap[kMaxBatch];
+    CUtensorMap tside[kMaxBatch];
+    LbmDev dev[kMaxBatch];
+    void* dst[kMaxBatch];
+    int* err[kMaxBatch];
+    int strip_chunks[kMaxBatch];
+    int first[kMaxBatch + 1];
+    int n;
+};
+cudaError_t prepare_stream();
+bool stream_eligible(const LbmDev& d);
+int stream_columns(const LbmDev& d);
+// chunks per strip when `columns` kTileX-wide columns share the launch
+int stream_strip_chunks(const LbmDev& d, int columns, int num_sms);
+int stream_blocks(const LbmDev& d, int strip_chunks);
+cudaError_t launch_stream_batch(const StreamBatchArgs& args, cudaStream_t s);
+
 cudaError_t launch_analytic_fields(const LbmDev& d, float* fields, cudaStream_t s);
 cudaError_t launch_init_equilibrium(const LbmDev& d, const float* fields, float* pops,
                                     cudaStream_t s);

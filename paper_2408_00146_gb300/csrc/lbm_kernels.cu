@@ -328,6 +328,13 @@ __device__ __forceinline__ int wrap_x(const LbmDev& d, int x)
 
 // ---- per-tile pieces shared by the step kernels -------------------------------------
 
+// The 36 staged populations of one node: p[a * stride], a = 9 set + alpha.
+struct OwnPops {
+    const float* p;
+    int stride;
+    __device__ __forceinline__ float operator()(int a) const { return p[a * stride]; }
+};
+
 // Shared-memory views of one tile: its own populations [36][TY][TX] and the
 // macroscopic fields on the tile plus halo (phi with two nodes of halo, the
 // rest with one).
@@ -347,24 +354,46 @@ struct NodeMoments {
 // Moments of the own node (Eqs. (28), (34), (39), (44)) from the staged
 // populations; phi, sigma(T, psi) and p* - rho c_s^2 go to the field tiles.
 // side != 0: the slot holds a wall mirror, whose temperature is 2 T_w - T.
-__device__ __forceinline__ NodeMoments own_moments(const LbmDev& d, const TileSmem& sm, int tx,
-                                                   int ty, int side)
+// Zeroth moments of the four sets and the first moments of g at one node.
+__device__ __forceinline__ NodeMoments pop_moments(const OwnPops& own)
 {
     NodeMoments m;
     float v[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = sm.pop[a][ty][tx];
+    for (int a = 0; a < 9; ++a) v[a] = own(a);
     m.phi = sum9(v);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = sm.pop[9 + a][ty][tx];
+    for (int a = 0; a < 9; ++a) v[a] = own(9 + a);
     m.pst = sum9(v);
     m.jx = mx9(v);
     m.jy = my9(v);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = sm.pop[18 + a][ty][tx];
+    for (int a = 0; a < 9; ++a) v[a] = own(18 + a);
     m.T = sum9(v);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = sm.pop[27 + a][ty][tx];
+    for (int a = 0; a < 9; ++a) v[a] = own(27 + a);
+    m.psi = sum9(v);
+    return m;
+}
+
+__device__ __forceinline__ NodeMoments own_moments(const LbmDev& d, const TileSmem& sm,
+                                                   const OwnPops& own, int tx, int ty, int side)
+{
+    NodeMoments m;
+    float v[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = own(a);
+    m.phi = sum9(v);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = own(9 + a);
+    m.pst = sum9(v);
+    m.jx = mx9(v);
+    m.jy = my9(v);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = own(18 + a);
+    m.T = sum9(v);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = own(27 + a);
     m.psi = sum9(v);
     float Tg = m.T;
     if (side < 0) Tg = 2.0f * d.T_H - m.T;
@@ -424,9 +453,9 @@ struct StoreF32 {
 // collisions and the push to the neighbours (or, in kFields mode, the fields).
 template <int kMode, class Store>
 __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
-                                            const NodeMoments& m, const Store& st,
-                                            float* __restrict__ fdst, int tx, int ty, int gx,
-                                            int gy)
+                                            const NodeMoments& m, const OwnPops& own,
+                                            const Store& st, float* __restrict__ fdst, int tx,
+                                            int ty, int gx, int gy)
 {
     const int N = d.nx * d.ny;
     const int r = ty + 1, c = tx + 1;
@@ -474,7 +503,7 @@ __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
     // ---- f: conservative Allen-Cahn (App. B) ---------------------------------------
     {
 #pragma unroll
-        for (int a = 0; a < 9; ++a) v[a] = sm.pop[a][ty][tx];
+        for (int a = 0; a < 9; ++a) v[a] = own(a);
         const float theta_m = d.mphi_4_over_W * phi * (1.0f - phi);   // M_phi theta
         scalar_collide(v, phi, theta_m * n_x, theta_m * n_y, d.omega_phi, ux, uy);
         Mf = st.template put<false>(0, N, nb, v, phi, wall, 0.0f);
@@ -482,7 +511,7 @@ __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
     // ---- h: energy (App. D), rate from the local thermal diffusivity -----------------
     {
 #pragma unroll
-        for (int a = 0; a < 9; ++a) v[a] = sm.pop[18 + a][ty][tx];
+        for (int a = 0; a < 9; ++a) v[a] = own(18 + a);
         const float alpha = d.alphaA + phi * d.dalpha;
         const float wT = 1.0f / (3.0f * alpha + 0.5f);
         scalar_collide(v, T, 0.0f, 0.0f, wT, ux, uy);
@@ -491,7 +520,7 @@ __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
     // ---- q: surfactant (App. E) -------------------------------------------------
     {
 #pragma unroll
-        for (int a = 0; a < 9; ++a) v[a] = sm.pop[27 + a][ty][tx];
+        for (int a = 0; a < 9; ++a) v[a] = own(27 + a);
         const float dG = (phi - 0.5f) * (d.g_s32 * phi * (1.0f - phi) + d.g_w);
         const float flux = -d.m_psi * psi * (1.0f - psi) * dG;   // times grad phi
         scalar_collide(v, psi, flux * gpx, flux * gpy, d.omega_psi, ux, uy);
@@ -500,7 +529,7 @@ __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
     // ---- g: two-fluid pressure/velocity (App. C) ----------------------------------------
     {
 #pragma unroll
-        for (int a = 0; a < 9; ++a) v[a] = sm.pop[9 + a][ty][tx];
+        for (int a = 0; a < 9; ++a) v[a] = own(9 + a);
         const float mu = d.muA + phi * d.dmu;
         const float wn = 1.0f / (3.0f * mu * inv_rho + 0.5f);
         const float vp = p - rho * kCs2;                      // varphi = p - rho c_s^2
@@ -638,12 +667,13 @@ __device__ __forceinline__ void step_tile(const LbmDev& d, const float* __restri
             return;
         }
     }
-    const NodeMoments m = own_moments(d, sm, tx, ty, own_side);
+    const OwnPops own{&s_pop[0][ty][tx], TX * TY};
+    const NodeMoments m = own_moments(d, sm, own, tx, ty, own_side);
     __syncthreads();
     normals_pass(sm, tid, TX * TY);
     __syncthreads();
     if (!active) return;
-    node_update<kMode>(d, sm, m, StoreF32{dst}, dst, tx, ty, gx, gy);
+    node_update<kMode>(d, sm, m, own, StoreF32{dst}, dst, tx, ty, gx, gy);
 }
 
 template <int kMode, bool kTma>
@@ -976,12 +1006,13 @@ __device__ __forceinline__ void step_tile_dev(const LbmDev& d, const S* __restri
         halo_fields(d, sm, ex, ey, ring1, side, sums[0], sums[1], sums[2], sums[3]);
     }
 
-    const NodeMoments m = own_moments(d, sm, tx, ty, own_side);
+    const OwnPops own{&s_pop[0][ty][tx], TX * TY};
+    const NodeMoments m = own_moments(d, sm, own, tx, ty, own_side);
     __syncthreads();
     normals_pass(sm, tid, TX * TY);
     __syncthreads();
     if (!active) return;
-    node_update<kMode>(d, sm, m, StoreDev<S>{ddst, mdst}, fdst, tx, ty, gx, gy);
+    node_update<kMode>(d, sm, m, own, StoreDev<S>{ddst, mdst}, fdst, tx, ty, gx, gy);
 }
 
 constexpr int kDevPopSmem = 36 * kTileX * kTileY * sizeof(float);  // dynamic shared memory
@@ -1006,6 +1037,254 @@ __global__ void __launch_bounds__(kTileX * kTileY, 4)
                             static_cast<const float4*>(args.msrc[s]), static_cast<S*>(args.dst[s]),
                             static_cast<float4*>(args.mdst[s]), nullptr, t % tiles_x,
                             t / tiles_x);
+}
+
+// ---- streaming along y (FP32 storage, walls) -----------------------------------------
+//
+// A block owns one kTileX-wide column of the lattice over a range of 8-row
+// chunks (a strip) and walks it in +y.  Each chunk's populations, and the
+// four columns on either side of it, arrive by TMA one chunk ahead into the
+// other of two stages while the current chunk is processed.  The macroscopic
+// fields live in a 12-row window that rolls with the chunks, so the rows
+// above and below a chunk are never loaded a second time: they are rows of
+// the previous and of the current chunk.  Updating a chunk's top two rows
+// needs fields two rows further up, so those two rows are updated one
+// iteration later, from a copy of their populations (the carry).  Rows beyond
+// a wall take their fields from the mirrored fluid row, as in src_row.
+constexpr int kSideW = 4;                 // side box width: 16 bytes of FP32
+constexpr int kWin = kTileY + 4;          // rows of the field window
+
+struct StreamSmem {
+    float pop[2][36][kTileY][kTileX];           // stages: the chunk's populations
+    float side[2][2][36][kTileY][kSideW];       // stages: left and right side boxes
+    float carry[36][2][kTileX];                 // populations of the two lagging rows
+    __align__(16) float phi[kWin][kTileX + 4];  // window row j: physical row base + j
+    __align__(16) float phs[kWin][kTileX + 2];  // p* - rho c_s^2
+    __align__(16) float T[kWin][kTileX + 2];    // T (mirror rows: 2 T_w - T)
+    __align__(16) float psi[kWin][kTileX + 2];
+    __align__(16) float sig[kWin][kTileX + 2];
+    __align__(16) float nrmx[kWin - 2][kTileX + 2];   // row i: window row i + 1
+    __align__(16) float nrmy[kWin - 2][kTileX + 2];
+    uint64_t bar[2];
+};
+constexpr int kStreamSmem = (int)sizeof(StreamSmem);
+constexpr int kSideItems = 10 * kTileY;   // 8 rows x (2 outer + 2 x 4 inner) items
+constexpr uint32_t kStreamStageBytes =
+    (36u * kTileY * kTileX + 2u * 36u * kTileY * kSideW) * (uint32_t)sizeof(float);
+
+// One strip: block-local index lb is column lb % ncol, strip lb / ncol, of
+// strip_chunks chunks.
+__device__ __forceinline__ void stream_strip(const LbmDev& d, float* __restrict__ dst,
+                                             const CUtensorMap* tmap, const CUtensorMap* tside,
+                                             int strip_chunks, int* __restrict__ err, int lb)
+{
+    extern __shared__ __align__(128) unsigned char s_raw[];
+    StreamSmem& S = *reinterpret_cast<StreamSmem*>(s_raw);
+    constexpr int NT = kTileX * kTileY;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTileX + tx;
+    const int ncol = d.nx / kTileX;
+    const int x0 = (lb % ncol) * kTileX;
+    const int nchunks = (d.nfy + kTileY - 1) / kTileY;
+    const int c0 = (lb / ncol) * strip_chunks;
+    const int c1 = min(c0 + strip_chunks, nchunks);
+    if (c0 >= c1) return;
+    const int xl = x0 == 0 ? d.nx - kSideW : x0 - kSideW;
+    const int xr = x0 + kTileX == d.nx ? 0 : x0 + kTileX;
+    // chunk c0 - 1 is read only for its fields and its top two rows (whose
+    // update this strip owns); the last strip ends with an iteration that
+    // has no chunk and updates the final carry
+    const int kfirst = c0 > 0 ? c0 - 1 : 0;
+    const int klast = c1 == nchunks ? c1 : c1 - 1;
+    const TileSmem sm{nullptr, S.phi, &S.sig[1], &S.phs[1], S.nrmx, S.nrmy};
+
+    if (tid == 0) {
+        mbar_init(smem_addr(&S.bar[0]), 1);
+        mbar_init(smem_addr(&S.bar[1]), 1);
+    }
+    __syncthreads();
+    auto issue = [&](int k) {   // chunk k into stage k & 1 (one thread)
+        const int st = k & 1;
+        const uint32_t bar = smem_addr(&S.bar[st]);
+        const int y = d.y0 + k * kTileY;
+        mbar_expect_tx(bar, kStreamStageBytes);
+        tma_load_tile(smem_addr(&S.pop[st][0][0][0]), tmap, x0, y, bar);
+        tma_load_tile(smem_addr(&S.side[st][0][0][0][0]), tside, xl, y, bar);
+        tma_load_tile(smem_addr(&S.side[st][1][0][0][0]), tside, xr, y, bar);
+    };
+    if (tid == 0) {
+        issue(kfirst);
+        if (kfirst + 1 < c1) issue(kfirst + 1);
+    }
+    uint32_t parity = 0;        // bit st: wait parity of stage st
+
+    // node of the chunk whose moments this thread computes: row (ty + 6) % 8,
+    // so that for ty >= 2 it is the node the thread updates in the same
+    // iteration (chunk row ty - 2)
+    const int rb = (ty + kTileY - 2) % kTileY;
+    for (int k = kfirst; k <= klast; ++k) {
+        const bool have = k < c1;
+        const int st = k & 1;
+        const int base = d.y0 + k * kTileY - 4;     // physical row of window row 0
+        const bool walled = base < 1 || base + kWin - 1 > d.ny - 2;
+        NodeMoments m{};
+        if (have) {
+            const bool ok = mbar_wait_bounded(smem_addr(&S.bar[st]), (parity >> st) & 1u);
+            parity ^= 1u << st;
+            if (__syncthreads_or(!ok)) {
+                // a copy did not arrive in time: report it, and keep the block
+                // resident for one more bounded wait on each stage so that no
+                // transfer into its shared memory outlives it
+                if (tid == 0) {
+                    atomicExch(err, 1);
+                    mbar_wait_bounded(smem_addr(&S.bar[st]), ((parity >> st) & 1u) ^ 1u);
+                    if (k + 1 < c1)
+                        mbar_wait_bounded(smem_addr(&S.bar[st ^ 1]), (parity >> (st ^ 1)) & 1u);
+                }
+                return;
+            }
+            // fields of the chunk's rows (window rows 4..11)
+            m = pop_moments(OwnPops{&S.pop[st][0][rb][tx], kTileY * kTileX});
+            S.phi[4 + rb][tx + 2] = m.phi;
+            S.phs[4 + rb][tx + 1] = m.pst - (d.rhoA + m.phi * d.drho) * kCs2;
+            S.T[4 + rb][tx + 1] = m.T;
+            S.psi[4 + rb][tx + 1] = m.psi;
+            if (tid < kSideItems) {
+                // side nodes x0-2, x0+33 (phi only) and x0-1, x0+32 (phi,
+                // p* - rho c_s^2, T, psi): one (node, field) item per thread
+                const int r = tid % kTileY, item = tid / kTileY;   // item 0..9
+                const bool outer = item < 2;
+                const int lr = outer ? item : (item - 2) / 4;      // 0 left, 1 right
+                const int f = outer ? 0 : (item - 2) % 4;          // field
+                const int bc = outer ? (lr ? 1 : 2) : (lr ? 0 : 3);
+                const float* sp = &S.side[st][lr][0][r][bc];
+                constexpr int P = kTileY * kSideW;                 // plane stride
+                float v[9];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) v[a] = sp[(9 * (f == 1 ? 0 : f) + a) * P];
+                const float sf = sum9(v);
+                const int c = lr ? kTileX + 1 : 0;                 // column in the 34-wide arrays
+                if (outer) {
+                    S.phi[4 + r][lr ? kTileX + 3 : 0] = sf;
+                } else if (f == 0) {
+                    S.phi[4 + r][c + 1] = sf;
+                } else if (f == 1) {
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) v[a] = sp[(9 + a) * P];
+                    S.phs[4 + r][c] = sum9(v) - (d.rhoA + sf * d.drho) * kCs2;
+                } else if (f == 2) {
+                    S.T[4 + r][c] = sf;
+                } else {
+                    S.psi[4 + r][c] = sf;
+                }
+            }
+        }
+        __syncthreads();
+        // rows of the window beyond a wall: the mirrored fluid row's fields
+        if (walled) {
+            for (int i = tid; i < kWin * (kTileX + 4); i += NT) {
+                const int j = i / (kTileX + 4), c = i % (kTileX + 4);
+                const int y = base + j;
+                if (y >= 1 && y <= d.ny - 2) continue;
+                const int js = (y < 1 ? 1 - y : 2 * d.ny - 3 - y) - base;
+                if (js < 0 || js >= kWin) continue;
+                S.phi[j][c] = S.phi[js][c];
+                if (c >= 1 && c <= kTileX + 2) {
+                    S.phs[j][c - 1] = S.phs[js][c - 1];
+                    S.psi[j][c - 1] = S.psi[js][c - 1];
+                    S.T[j][c - 1] = 2.0f * (y < 1 ? d.T_H : d.T_C) - S.T[js][c - 1];
+                }
+            }
+            __syncthreads();
+        }
+        if (k >= c0) {
+            // normals and sigma on window rows 1..10; rows 1 and 2 were rows
+            // 9 and 10 of the previous iteration (rolled), unless this is the
+            // strip's first update or the window reaches a wall
+            const int j0 = (k == c0 || walled) ? 1 : 3;
+            for (int i = tid + (j0 - 1) * (kTileX + 2); i < (kWin - 2) * (kTileX + 2); i += NT) {
+                const int jr = i / (kTileX + 2), c = i % (kTileX + 2);
+                float gxp, gyp;
+                grad_smem<kTileX + 4>(S.phi, jr + 1, c + 1, gxp, gyp);
+                const float inv = 1.0f / fmaxf(sqrtf(gxp * gxp + gyp * gyp), kNormalEps);
+                S.nrmx[jr][c] = gxp * inv;
+                S.nrmy[jr][c] = gyp * inv;
+                S.sig[jr + 1][c] = sigma_eos(d, S.T[jr + 1][c], S.psi[jr + 1][c]);
+            }
+            __syncthreads();
+            // update window row ty + 2: the carry (ty < 2) or chunk row ty - 2
+            const int gy = base + ty + 2;
+            if (gy >= 1 && gy <= d.ny - 2 && (ty < 2 || have)) {
+                const OwnPops own = ty < 2 ? OwnPops{&S.carry[0][ty][tx], 2 * kTileX}
+                                           : OwnPops{&S.pop[st][0][ty - 2][tx], kTileY * kTileX};
+                if (ty < 2) m = pop_moments(own);
+                node_update<kStep>(d, sm, m, own, StoreF32{dst}, dst, tx, ty, x0 + tx, gy);
+            }
+        }
+        __syncthreads();
+        if (have) {
+            // the chunk's top two rows become the carry (16-byte copies)
+            for (int i = tid; i < 36 * 2 * kTileX / 4; i += NT) {
+                const int a = i / (2 * kTileX / 4), q = i % (2 * kTileX / 4);
+                reinterpret_cast<float4*>(&S.carry[a][0][0])[q] =
+                    reinterpret_cast<const float4*>(&S.pop[st][a][kTileY - 2][0])[q];
+            }
+        }
+        // the window rolls by 8 rows: rows 8..11 -> 0..3 (fields), 9..10 ->
+        // 1..2 (normals, sigma)
+        {
+            constexpr int W4 = kTileX + 4, W2 = kTileX + 2;
+            constexpr int n4 = 4 * W4 / 4, n2 = 4 * W2 / 4, m2 = 2 * W2 / 4;
+            static_assert((4 * W4) % 4 == 0 && (4 * W2) % 4 == 0 && (2 * W2) % 4 == 0,
+                          "whole float4 rows");
+            for (int i = tid; i < n4 + 3 * n2 + 3 * m2; i += NT) {
+                if (i < n4) {
+                    reinterpret_cast<float4*>(&S.phi[0][0])[i] =
+                        reinterpret_cast<const float4*>(&S.phi[kTileY][0])[i];
+                    continue;
+                }
+                int q = i - n4;
+                if (q < 3 * n2) {
+                    float(*arr)[W2] = q < n2 ? S.phs : (q < 2 * n2 ? S.T : S.psi);
+                    q %= n2;
+                    reinterpret_cast<float4*>(&arr[0][0])[q] =
+                        reinterpret_cast<const float4*>(&arr[kTileY][0])[q];
+                    continue;
+                }
+                q -= 3 * n2;
+                const int w = q / m2;
+                q %= m2;
+                if (w == 0) {
+                    // sig rows 1 and 9 start 8 bytes past a 16-byte boundary
+                    reinterpret_cast<float2*>(&S.sig[1][0])[2 * q] =
+                        reinterpret_cast<const float2*>(&S.sig[kTileY + 1][0])[2 * q];
+                    reinterpret_cast<float2*>(&S.sig[1][0])[2 * q + 1] =
+                        reinterpret_cast<const float2*>(&S.sig[kTileY + 1][0])[2 * q + 1];
+                } else if (w == 1) {
+                    reinterpret_cast<float4*>(&S.nrmx[0][0])[q] =
+                        reinterpret_cast<const float4*>(&S.nrmx[kTileY][0])[q];
+                } else {
+                    reinterpret_cast<float4*>(&S.nrmy[0][0])[q] =
+                        reinterpret_cast<const float4*>(&S.nrmy[kTileY][0])[q];
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && k + 2 < c1) issue(k + 2);
+    }
+}
+
+// Streaming step of up to kMaxBatch simulations in one launch: block b runs
+// strip b - first[s] of simulation s (first[s] <= b < first[s + 1]).  A
+// single simulation's step is a batch of one, so a simulation steps through
+// the same code whether it is batched or not.
+__global__ void __launch_bounds__(kTileX * kTileY, 2)
+    stream_batch_kernel(const __grid_constant__ StreamBatchArgs args)
+{
+    int s = 0;
+    while (s + 1 < args.n && (int)blockIdx.x >= args.first[s + 1]) ++s;
+    stream_strip(args.dev[s], static_cast<float*>(args.dst[s]), &args.tmap[s], &args.tside[s],
+                 args.strip_chunks[s], args.err[s], blockIdx.x - args.first[s]);
 }
 
 // Source node of population a at fluid node (x, y) for the rest-state
@@ -1395,5 +1674,41 @@ cudaError_t launch_join_planes(const LbmDev& d, int precision, const void* dev, 
             d, static_cast<const __nv_bfloat16*>(dev), mom, a0, count, planes);
     else
         return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_stream()
+{
+    return cudaFuncSetAttribute(stream_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kStreamSmem);
+}
+
+bool stream_eligible(const LbmDev& d)
+{
+    return d.walls && d.nx % kTileX == 0 && d.nfy >= 2 * kTileY;
+}
+
+int stream_columns(const LbmDev& d) { return d.nx / kTileX; }
+
+int stream_strip_chunks(const LbmDev& d, int columns, int num_sms)
+{
+    const int nchunks = (d.nfy + kTileY - 1) / kTileY;
+    // at most two blocks per SM over the columns of the whole launch (one
+    // wave, no tail of late strips), and strips of at least four chunks (the
+    // chunk before each strip is read twice)
+    const int strips = max(1, (2 * num_sms) / max(columns, 1));
+    return max(4, (nchunks + strips - 1) / strips);
+}
+
+int stream_blocks(const LbmDev& d, int strip_chunks)
+{
+    const int ncol = d.nx / kTileX;
+    const int nchunks = (d.nfy + kTileY - 1) / kTileY;
+    return ncol * ((nchunks + strip_chunks - 1) / strip_chunks);
+}
+
+cudaError_t launch_stream_batch(const StreamBatchArgs& args, cudaStream_t s)
+{
+    stream_batch_kernel<<<args.first[args.n], dim3(kTileX, kTileY), kStreamSmem, s>>>(args);
     return cudaGetLastError();
 }
