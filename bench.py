@@ -79,20 +79,28 @@ def kernel_hash() -> str:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def step_kernel_name(mode: str, precision: str) -> str:
+def streams(p: dict) -> bool:
+    """Whether the library steps this FP32 lattice with the y-streaming
+    kernel (walls, nx a multiple of 32, at least 16 fluid rows)."""
+    return bool(p["walls"]) and p["nx"] % 32 == 0 and p["ny"] - 2 >= 16
+
+
+def step_kernel_name(mode: str, precision: str, params=None) -> str:
     if precision == "fp32":
+        if params and all(streams(p) for p in params):
+            return "stream_batch_kernel"
         return "step_batch_kernel" if mode == "batched" else "step_kernel"
     return "step_batch_dev_kernel" if mode == "batched" else "step_dev_kernel"
 
 
-def profiled_traffic(work: str, mode: str, precision: str):
+def profiled_traffic(work: str, mode: str, precision: str, params=None):
     """DRAM bytes per step-kernel launch from the committed ncu summary, if it
     was taken on the current kernel source for this workload and launch."""
     if not os.path.exists(PROFILE_TRAFFIC):
         return None
     with open(PROFILE_TRAFFIC) as fh:
         d = json.load(fh)
-    ent = d.get(f"{work}/{precision}/{step_kernel_name(mode, precision)}")
+    ent = d.get(f"{work}/{precision}/{step_kernel_name(mode, precision, params)}")
     if not ent or ent.get("kernel_sha256_16") != kernel_hash():
         return None
     return float(ent["dram_bytes_per_launch"])
@@ -304,8 +312,8 @@ def run_gpu(args) -> None:
     per_launch_bytes = bpn * nodes_per_step / len(params) * sims_per_launch
     peaks = measured_peaks()
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-    kernel = step_kernel_name(args.mode, args.precision)
-    traffic = profiled_traffic(args.workload, args.mode, args.precision)
+    kernel = step_kernel_name(args.mode, args.precision, params)
+    traffic = profiled_traffic(args.workload, args.mode, args.precision, params)
 
     # the other launch mode on the same simulations, for comparison
     other = None
