@@ -5,8 +5,8 @@ elasticity beta in {0.05, 0.1, 0.2} x quadratic sensitivity sigma_TT in
 {5e-4, 1e-3, 2e-3}, bubble R=32 a quarter of the way along the channel,
 density ratio 10, FP32 storage.  One benchmark step advances every
 simulation of the batch by one time step: by default one launch of the
-batched step kernel over all nine (--mode plain: nine launches, one per
-simulation).  Each simulation's 75 MB state has been evicted from the 129 MB
+batched streaming step kernel over all nine (--mode plain: nine launches,
+one per simulation).  Each simulation's 75 MB state has been evicted from the 129 MB
 L2 by the other eight before it is read again.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
