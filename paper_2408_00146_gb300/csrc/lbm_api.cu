@@ -12,6 +12,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <functional>
+#include <vector>
+#include <algorithm>
+#include <utility>
 
 namespace {
 
@@ -257,6 +261,83 @@ bool encode_population_maps(lbm_sim* s)
 
 const CUtensorMap* map_of(const lbm_sim* s, int buf) { return s->have_tmap ? &s->tmap[buf] : nullptr; }
 
+// Strip lengths for one streaming launch over n lattices.  A strip of L
+// chunks costs about L + 2 chunk-times (the chunk below it is read first,
+// plus start-up); strips run on 2 x num_sms block slots in launch order,
+// longest first.  For each candidate target length the strips are placed by
+// that rule (a slot takes the next strip when it frees) and the candidate
+// with the shortest predicted launch wins; a lattice with fewer chunks than
+// the target takes whole columns.  The prediction is cached for the last
+// few size lists, since lbm_step_batch may be called once per step.
+void plan_strips(const LbmDev* const* devs, int n, int num_sms, int* out)
+{
+    struct Entry {
+        int n = -1, sms = 0;
+        int nchunks[kMaxBatch], ncol[kMaxBatch], plan[kMaxBatch];
+    };
+    static thread_local Entry cache[8];
+    static thread_local int next = 0;
+    int nch[kMaxBatch], ncol[kMaxBatch], maxch = 1;
+    for (int i = 0; i < n; ++i) {
+        nch[i] = (devs[i]->nfy + kTileY - 1) / kTileY;
+        ncol[i] = stream_columns(*devs[i]);
+        maxch = std::max(maxch, nch[i]);
+    }
+    for (Entry& e : cache) {
+        if (e.n != n || e.sms != num_sms) continue;
+        bool same = true;
+        for (int i = 0; i < n && same; ++i) same = e.nchunks[i] == nch[i] && e.ncol[i] == ncol[i];
+        if (same) {
+            std::memcpy(out, e.plan, sizeof(int) * n);
+            return;
+        }
+    }
+    const int slots = 2 * std::max(num_sms, 1);
+    std::vector<int> cand = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+    for (int k = 1; k <= 16; ++k) cand.push_back((maxch + k - 1) / k);
+    double best = 1e300;
+    int best_plan[kMaxBatch];
+    std::vector<int> lens;
+    std::vector<double> load;
+    for (int L : cand) {
+        if (L < 4 || L > maxch) continue;
+        int plan[kMaxBatch];
+        lens.clear();
+        for (int i = 0; i < n; ++i) {
+            const int ns = (nch[i] + L - 1) / L;
+            plan[i] = std::max(4, (nch[i] + ns - 1) / ns);
+            const int per_col = (nch[i] + plan[i] - 1) / plan[i];
+            for (int c = 0; c < ncol[i]; ++c)
+                for (int t = 0; t < per_col; ++t)
+                    lens.push_back(std::min(plan[i], nch[i] - t * plan[i]));
+        }
+        std::sort(lens.begin(), lens.end(), std::greater<int>());
+        load.assign(slots, 0.0);
+        std::make_heap(load.begin(), load.end(), std::greater<double>());
+        double span = 0.0;
+        for (int l : lens) {
+            std::pop_heap(load.begin(), load.end(), std::greater<double>());
+            load.back() += l + 2.0;
+            span = std::max(span, load.back());
+            std::push_heap(load.begin(), load.end(), std::greater<double>());
+        }
+        if (span < best - 1e-9) {
+            best = span;
+            std::memcpy(best_plan, plan, sizeof(int) * n);
+        }
+    }
+    if (best == 1e300)
+        for (int i = 0; i < n; ++i) best_plan[i] = std::max(4, nch[i]);
+    Entry& e = cache[next];
+    next = (next + 1) % 8;
+    e.n = n;
+    e.sms = num_sms;
+    std::memcpy(e.nchunks, nch, sizeof(int) * n);
+    std::memcpy(e.ncol, ncol, sizeof(int) * n);
+    std::memcpy(e.plan, best_plan, sizeof(int) * n);
+    std::memcpy(out, best_plan, sizeof(int) * n);
+}
+
 }  // namespace
 
 static lbm_status create_impl(const lbm_params* p, void* stream, void* ws, size_t ws_bytes,
@@ -314,7 +395,8 @@ static lbm_status create_impl(const lbm_params* p, void* stream, void* ws, size_
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
         if (e == cudaSuccess) e = prepare_stream();
         s->num_sms = sms > 0 ? sms : 1;
-        s->strip_chunks = stream_strip_chunks(s->dev, stream_columns(s->dev), s->num_sms);
+        const LbmDev* one = &s->dev;
+        plan_strips(&one, 1, s->num_sms, &s->strip_chunks);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s->h_res), 16 * sizeof(double));
@@ -588,7 +670,7 @@ lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
     int tiles[3] = {0, 0, 0};
     lbm_sim* group[3][kMaxBatch];
     lbm_sim* sgroup[kMaxBatch];
-    int sn = 0, scols = 0;
+    int sn = 0;
     for (int k = 0; k < 3; ++k) {
         args[k].n = 0;
         args[k].first[0] = 0;
@@ -596,7 +678,6 @@ lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
     for (int i = 0; i < n; ++i) {
         if (sims[i]->ystream) {
             sgroup[sn++] = sims[i];
-            scols += stream_columns(sims[i]->dev);
             continue;
         }
         const int k = sims[i]->p.precision;
@@ -609,8 +690,18 @@ lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
         a.n += 1;
     }
     int schunks[kMaxBatch];
-    for (int i = 0; i < sn; ++i)
-        schunks[i] = stream_strip_chunks(sgroup[i]->dev, scols, sgroup[i]->num_sms);
+    if (sn > 0) {
+        const LbmDev* devs[kMaxBatch];
+        for (int i = 0; i < sn; ++i) devs[i] = &sgroup[i]->dev;
+        plan_strips(devs, sn, sgroup[0]->num_sms, schunks);
+    }
+    // longest strips first: blocks start in index order, so the short ones
+    // fill the tail of the launch
+    for (int i = 1; i < sn; ++i)
+        for (int j = i; j > 0 && schunks[j] > schunks[j - 1]; --j) {
+            std::swap(schunks[j], schunks[j - 1]);
+            std::swap(sgroup[j], sgroup[j - 1]);
+        }
     for (int64_t step = 0; step < nsteps; ++step) {
         if (sn > 0) {
             sargs.n = sn;

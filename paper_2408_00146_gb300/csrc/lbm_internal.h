@@ -108,8 +108,6 @@ struct StreamBatchArgs {
 cudaError_t prepare_stream();
 bool stream_eligible(const LbmDev& d);
 int stream_columns(const LbmDev& d);
-// chunks per strip when `columns` kTileX-wide columns share the launch
-int stream_strip_chunks(const LbmDev& d, int columns, int num_sms);
 int stream_blocks(const LbmDev& d, int strip_chunks);
 cudaError_t launch_stream_batch(const StreamBatchArgs& args, cudaStream_t s);
 

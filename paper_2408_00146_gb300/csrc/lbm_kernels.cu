@@ -1690,16 +1690,6 @@ bool stream_eligible(const LbmDev& d)
 
 int stream_columns(const LbmDev& d) { return d.nx / kTileX; }
 
-int stream_strip_chunks(const LbmDev& d, int columns, int num_sms)
-{
-    const int nchunks = (d.nfy + kTileY - 1) / kTileY;
-    // at most two blocks per SM over the columns of the whole launch (one
-    // wave, no tail of late strips), and strips of at least four chunks (the
-    // chunk before each strip is read twice)
-    const int strips = max(1, (2 * num_sms) / max(columns, 1));
-    return max(4, (nchunks + strips - 1) / strips);
-}
-
 int stream_blocks(const LbmDev& d, int strip_chunks)
 {
     const int ncol = d.nx / kTileX;
