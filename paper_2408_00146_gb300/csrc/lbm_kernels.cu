@@ -335,6 +335,12 @@ struct OwnPops {
     __device__ __forceinline__ float operator()(int a) const { return p[a * stride]; }
 };
 
+// The same, held in registers (a fully unrolled local array).
+struct OwnRegs {
+    const float* v;
+    __device__ __forceinline__ float operator()(int a) const { return v[a]; }
+};
+
 // Shared-memory views of one tile: its own populations [36][TY][TX] and the
 // macroscopic fields on the tile plus halo (phi with two nodes of halo, the
 // rest with one).
@@ -355,7 +361,8 @@ struct NodeMoments {
 // populations; phi, sigma(T, psi) and p* - rho c_s^2 go to the field tiles.
 // side != 0: the slot holds a wall mirror, whose temperature is 2 T_w - T.
 // Zeroth moments of the four sets and the first moments of g at one node.
-__device__ __forceinline__ NodeMoments pop_moments(const OwnPops& own)
+template <class Own>
+__device__ __forceinline__ NodeMoments pop_moments(const Own& own)
 {
     NodeMoments m;
     float v[9];
@@ -451,9 +458,9 @@ struct StoreF32 {
 
 // Stencils, forces, velocity and pressure (Sec. 3, App. C), then the four
 // collisions and the push to the neighbours (or, in kFields mode, the fields).
-template <int kMode, class Store>
+template <int kMode, class Store, class Own>
 __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
-                                            const NodeMoments& m, const OwnPops& own,
+                                            const NodeMoments& m, const Own& own,
                                             const Store& st, float* __restrict__ fdst, int tx,
                                             int ty, int gx, int gy)
 {
@@ -1128,6 +1135,7 @@ __device__ __forceinline__ void stream_strip(const LbmDev& d, float* __restrict_
         const int base = d.y0 + k * kTileY - 4;     // physical row of window row 0
         const bool walled = base < 1 || base + kWin - 1 > d.ny - 2;
         NodeMoments m{};
+        float pv[36];
         if (have) {
             const bool ok = mbar_wait_bounded(smem_addr(&S.bar[st]), (parity >> st) & 1u);
             parity ^= 1u << st;
@@ -1144,7 +1152,9 @@ __device__ __forceinline__ void stream_strip(const LbmDev& d, float* __restrict_
                 return;
             }
             // fields of the chunk's rows (window rows 4..11)
-            m = pop_moments(OwnPops{&S.pop[st][0][rb][tx], kTileY * kTileX});
+#pragma unroll
+            for (int a = 0; a < 36; ++a) pv[a] = S.pop[st][a][rb][tx];
+            m = pop_moments(OwnRegs{pv});
             S.phi[4 + rb][tx + 2] = m.phi;
             S.phs[4 + rb][tx + 1] = m.pst - (d.rhoA + m.phi * d.drho) * kCs2;
             S.T[4 + rb][tx + 1] = m.T;
@@ -1215,10 +1225,12 @@ __device__ __forceinline__ void stream_strip(const LbmDev& d, float* __restrict_
             // update window row ty + 2: the carry (ty < 2) or chunk row ty - 2
             const int gy = base + ty + 2;
             if (gy >= 1 && gy <= d.ny - 2 && (ty < 2 || have)) {
-                const OwnPops own = ty < 2 ? OwnPops{&S.carry[0][ty][tx], 2 * kTileX}
-                                           : OwnPops{&S.pop[st][0][ty - 2][tx], kTileY * kTileX};
-                if (ty < 2) m = pop_moments(own);
-                node_update<kStep>(d, sm, m, own, StoreF32{dst}, dst, tx, ty, x0 + tx, gy);
+                if (ty < 2) {
+#pragma unroll
+                    for (int a = 0; a < 36; ++a) pv[a] = S.carry[a][ty][tx];
+                    m = pop_moments(OwnRegs{pv});
+                }
+                node_update<kStep>(d, sm, m, OwnRegs{pv}, StoreF32{dst}, dst, tx, ty, x0 + tx, gy);
             }
         }
         __syncthreads();
