@@ -207,6 +207,17 @@ void lbm_destroy(lbm_sim* sim);
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* lbm_last_error(void);
 
+/* Diagnostic of the failure path of the kernels' waits: launches one block
+ * that waits, with the same bounded wait the step kernels use for their tile
+ * copies, on a barrier that nothing ever completes, giving up after limit_ns
+ * nanoseconds of wall time (0 < limit_ns <= 1e10; the step kernels use 1 s).
+ * *gave_up = 1 when the block abandoned the wait and returned -- what lets a
+ * step whose copy never lands report LBM_ETIMEOUT through lbm_observe instead
+ * of hanging the GPU -- and 0 otherwise.  Uses the current device and default
+ * stream and synchronises it.  The paper has no counterpart.
+ * Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_probe_bounded_wait(int64_t limit_ns, int32_t* gave_up);
+
 /* FP64 observable sums over the fluid nodes of a caller-provided device field
  * array, for callers that cannot allocate device memory where they call it:
  * code recording a stream into a CUDA graph, latency-critical loops that must

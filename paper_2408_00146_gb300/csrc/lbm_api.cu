@@ -453,6 +453,22 @@ void lbm_destroy(lbm_sim* s)
 
 const char* lbm_last_error(void) { return g_err; }
 
+lbm_status lbm_probe_bounded_wait(int64_t limit_ns, int32_t* gave_up)
+{
+    if (!gave_up || limit_ns <= 0 || limit_ns > 10000000000LL)
+        return fail(LBM_EINVAL, "need gave_up != NULL and 0 < limit_ns <= 1e10");
+    int* d_flag = nullptr;
+    CUDA_TRY(cudaMalloc(&d_flag, sizeof(int)));
+    cudaError_t e = cudaMemset(d_flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = launch_bounded_wait_probe((uint64_t)limit_ns, d_flag, nullptr);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d_flag);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "bounded-wait probe: %s", cudaGetErrorString(e));
+    *gave_up = h;
+    return LBM_OK;
+}
+
 lbm_status lbm_get_derived(const lbm_sim* s, double* out)
 {
     if (!s || !out) return fail(LBM_EINVAL, "NULL argument");

@@ -111,6 +111,10 @@ int stream_columns(const LbmDev& d);
 int stream_blocks(const LbmDev& d, int strip_chunks);
 cudaError_t launch_stream_batch(const StreamBatchArgs& args, cudaStream_t s);
 
+// Diagnostic: one block waits with the kernels' bounded wait (limit_ns) on a
+// barrier nothing completes and sets *flag = 1 when it gives up.
+cudaError_t launch_bounded_wait_probe(uint64_t limit_ns, int* flag, cudaStream_t s);
+
 cudaError_t launch_analytic_fields(const LbmDev& d, float* fields, cudaStream_t s);
 cudaError_t launch_init_equilibrium(const LbmDev& d, const float* fields, float* pops,
                                     cudaStream_t s);

@@ -230,13 +230,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: gives up after kMaxWaitPolls polls (each poll may suspend the
-// thread for a short hardware-chosen interval) instead of spinning forever.
-constexpr int kMaxWaitPolls = 1 << 22;
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ uint64_t global_ns()
 {
-    for (int i = 0; i < kMaxWaitPolls; ++i)
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: gives up once limit_ns of wall time have passed (checked
+// every 256 polls of the barrier), or after kMaxWaitPolls polls whatever the
+// timer says, instead of spinning forever.  A copy that never completes thus
+// costs its block about a second and an error flag, not a hung GPU.
+constexpr int kMaxWaitPolls = 1 << 24;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  uint64_t limit_ns = kWaitLimitNs)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (int i = 1; i < kMaxWaitPolls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 0 && global_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 
@@ -1712,5 +1727,25 @@ int stream_blocks(const LbmDev& d, int strip_chunks)
 cudaError_t launch_stream_batch(const StreamBatchArgs& args, cudaStream_t s)
 {
     stream_batch_kernel<<<args.first[args.n], dim3(kTileX, kTileY), kStreamSmem, s>>>(args);
+    return cudaGetLastError();
+}
+
+namespace {
+// One block waits, with the step kernels' bounded wait, on a barrier that
+// expects an arrival nothing makes; flag[0] = 1 if the wait gave up.
+__global__ void bounded_wait_probe_kernel(uint64_t limit_ns, int* flag)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_addr(&bar);
+    if (threadIdx.x == 0) mbar_init(b, 1);
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(b, 0, limit_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) *flag = 1;
+}
+}  // namespace
+
+cudaError_t launch_bounded_wait_probe(uint64_t limit_ns, int* flag, cudaStream_t s)
+{
+    bounded_wait_probe_kernel<<<1, 32, 0, s>>>(limit_ns, flag);
     return cudaGetLastError();
 }

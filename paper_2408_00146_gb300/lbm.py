@@ -56,7 +56,7 @@ EXPORTS = [
     "lbm_derive", "lbm_workspace_bytes", "lbm_create", "lbm_create_ex", "lbm_init", "lbm_step",
     "lbm_step_batch",
     "lbm_observe", "lbm_get_populations", "lbm_get_derived", "lbm_launch_count",
-    "lbm_destroy", "lbm_last_error", "lbm_reduce_observables_noalloc",
+    "lbm_destroy", "lbm_last_error", "lbm_reduce_observables_noalloc", "lbm_probe_bounded_wait",
 ]
 
 
@@ -107,6 +107,7 @@ def load() -> ctypes.CDLL:
             L.lbm_destroy.restype = None
             L.lbm_reduce_observables_noalloc.argtypes = [vp, ctypes.c_int32, ctypes.c_int32,
                                                          ctypes.c_int32, vp, vp]
+            L.lbm_probe_bounded_wait.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]
             L.lbm_last_error.argtypes = []
             L.lbm_last_error.restype = ctypes.c_char_p
             for name in EXPORTS:
@@ -225,6 +226,15 @@ def lbm_launch_count(sim) -> int:
 
 def lbm_destroy(sim):
     load().lbm_destroy(sim)
+
+
+def lbm_probe_bounded_wait(limit_ns: int) -> bool:
+    """True if a block waiting on a barrier that never completes gave up after
+    limit_ns nanoseconds (the kernels' bounded wait; see include/lbm.h)."""
+    flag = ctypes.c_int32(0)
+    _check(load().lbm_probe_bounded_wait(int(limit_ns), ctypes.byref(flag)),
+           "lbm_probe_bounded_wait")
+    return bool(flag.value)
 
 
 def lbm_reduce_observables_noalloc(d_fields_ptr: int, nx: int, ny: int, walls: int,
