@@ -202,9 +202,12 @@ def cpu_baseline(work: str, budget_s: float = 15.0) -> dict:
     rate1, used, dt1 = oracle_rate(params, 1, threads)
     steps = max(1, min(1000, int(budget_s / max(dt1, 1e-6))))
     rate, used, dt = oracle_rate(params, steps, threads)
+    # the same oracle on one core, for a few seconds
+    rate_1, _, dt_1 = oracle_rate(params, max(1, steps // max(used, 1) // 3), 1)
     return {"value": rate, "unit": "MLUPS", "cores": used, "kind": "oracle",
             "sample": f"{steps} FP64 time steps of the first lattice of the workload "
-                      f"({params['nx']}x{params['ny']}), {dt:.1f} s"}
+                      f"({params['nx']}x{params['ny']}), {dt:.1f} s",
+            "single_core_value": rate_1}
 
 
 def run_reference(args) -> None:
@@ -289,8 +292,12 @@ def run_gpu(args) -> None:
         barrier()
         l0 = sum(s.launches() for s in sims)
         ev0.record(stream)
-        for _ in range(nsteps):
-            step_all()
+        if args.graph and args.mode == "plain":
+            for s in sims:                   # all steps in one call: CUDA-graph replay
+                s.step(nsteps)
+        else:
+            for _ in range(nsteps):
+                step_all()
         ev1.record(stream)
         barrier()
         return ev0.elapsed_time(ev1), sum(s.launches() for s in sims) - l0
@@ -341,7 +348,8 @@ def run_gpu(args) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "lattices": [f"{p['nx']}x{p['ny']}" for p in params],
                        "sims_per_gpu": len(params), "fluid_nodes_per_step": nodes_per_step,
-                       "launch_mode": args.mode, "other_mode": other,
+                       "launch_mode": args.mode + (" graph" if args.graph and args.mode == "plain" else ""),
+                       "other_mode": other,
                        "storage": args.precision,
                        "l2": "working set %.0f MB > 129 MB L2; simulations interleaved per step"
                              % (sum(2 * BYTES_PER_NODE_BUFFER[args.precision] * p["nx"] * p["ny"]
@@ -442,6 +450,9 @@ def main():
                          "plain: one launch per simulation")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="population storage (arithmetic is FP32 in every case)")
+    ap.add_argument("--graph", action="store_true",
+                    help="plain mode: advance each simulation by all timed steps in one "
+                         "lbm_step call (replayed CUDA graphs of 64 steps)")
     ap.add_argument("--compare-modes", action="store_true", default=True)
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--no-e2e", action="store_true")
