@@ -449,7 +449,7 @@ __device__ __forceinline__ void normals_pass(const TileSmem& sm, int tid, int nt
         const int cx = i % RW, cy = i / RW;
         float gxp, gyp;
         grad_smem<kTileX + 4>(sm.phi, cy + 1, cx + 1, gxp, gyp);
-        const float inv = 1.0f / fmaxf(sqrtf(gxp * gxp + gyp * gyp), kNormalEps);
+        const float inv = fminf(rsqrtf(gxp * gxp + gyp * gyp), 1.0f / kNormalEps);
         sm.nrmx[cy][cx] = gxp * inv;
         sm.nrmy[cy][cx] = gyp * inv;
     }
@@ -497,7 +497,7 @@ __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
     const float deltas = d.deltas_coef * g2;
     const float phi = m.phi, T = m.T, psi = m.psi;
     const float rho = d.rhoA + phi * d.drho;
-    const float inv_rho = 1.0f / rho;
+    const float inv_rho = __fdividef(1.0f, rho);
     const float Ftx = deltas * (-sig * kappa * n_x + sgx - n_x * ndots) + d.Fext_x;
     const float Fty = deltas * (-sig * kappa * n_y + sgy - n_y * ndots) + d.Fext_y -
                       (rho - d.rhoA) * d.gravity;
@@ -535,7 +535,7 @@ __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
 #pragma unroll
         for (int a = 0; a < 9; ++a) v[a] = own(18 + a);
         const float alpha = d.alphaA + phi * d.dalpha;
-        const float wT = 1.0f / (3.0f * alpha + 0.5f);
+        const float wT = __fdividef(1.0f, 3.0f * alpha + 0.5f);
         scalar_collide(v, T, 0.0f, 0.0f, wT, ux, uy);
         Mh = st.template put<true>(2, N, nb, v, T, wall, wall < 0 ? d.T_H : d.T_C);
     }
@@ -553,7 +553,7 @@ __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
 #pragma unroll
         for (int a = 0; a < 9; ++a) v[a] = own(9 + a);
         const float mu = d.muA + phi * d.dmu;
-        const float wn = 1.0f / (3.0f * mu * inv_rho + 0.5f);
+        const float wn = __fdividef(1.0f, 3.0f * mu * inv_rho + 0.5f);
         const float vp = p - rho * kCs2;                      // varphi = p - rho c_s^2
         const float ux2 = ux * ux, uy2 = uy * uy;
         float cm[9];
@@ -1090,7 +1090,7 @@ struct StreamSmem {
     uint64_t bar[2];
 };
 constexpr int kStreamSmem = (int)sizeof(StreamSmem);
-constexpr int kSideItems = 10 * kTileY;   // 8 rows x (2 outer + 2 x 4 inner) items
+constexpr int kSideItems = 6 * kTileY;    // 8 rows x (2 outer + 2 x 2 inner) items
 constexpr uint32_t kStreamStageBytes =
     (36u * kTileY * kTileX + 2u * 36u * kTileY * kSideW) * (uint32_t)sizeof(float);
 
@@ -1174,33 +1174,37 @@ __device__ __forceinline__ void stream_strip(const LbmDev& d, float* __restrict_
             S.phs[4 + rb][tx + 1] = m.pst - (d.rhoA + m.phi * d.drho) * kCs2;
             S.T[4 + rb][tx + 1] = m.T;
             S.psi[4 + rb][tx + 1] = m.psi;
-            if (tid < kSideItems) {
-                // side nodes x0-2, x0+33 (phi only) and x0-1, x0+32 (phi,
-                // p* - rho c_s^2, T, psi): one (node, field) item per thread
-                const int r = tid % kTileY, item = tid / kTileY;   // item 0..9
+            S.sig[4 + rb][tx + 1] = sigma_eos(d, m.T, m.psi);
+            if (tid >= NT - kSideItems) {
+                // side nodes x0-2, x0+33 (phi) and x0-1, x0+32 (phi and
+                // p* - rho c_s^2; T, psi and sigma): one item per thread
+                const int it = tid - (NT - kSideItems);
+                const int r = it % kTileY, item = it / kTileY;     // item 0..5
                 const bool outer = item < 2;
-                const int lr = outer ? item : (item - 2) / 4;      // 0 left, 1 right
-                const int f = outer ? 0 : (item - 2) % 4;          // field
+                const int lr = outer ? item : (item - 2) / 2;      // 0 left, 1 right
+                const int f = outer ? 0 : (item - 2) % 2;          // 0: sets f, g; 1: h, q
                 const int bc = outer ? (lr ? 1 : 2) : (lr ? 0 : 3);
-                const float* sp = &S.side[st][lr][0][r][bc];
+                const float* sp = &S.side[st][lr][f * 18][r][bc];
                 constexpr int P = kTileY * kSideW;                 // plane stride
                 float v[9];
 #pragma unroll
-                for (int a = 0; a < 9; ++a) v[a] = sp[(9 * (f == 1 ? 0 : f) + a) * P];
-                const float sf = sum9(v);
+                for (int a = 0; a < 9; ++a) v[a] = sp[a * P];
+                const float s1 = sum9(v);
                 const int c = lr ? kTileX + 1 : 0;                 // column in the 34-wide arrays
                 if (outer) {
-                    S.phi[4 + r][lr ? kTileX + 3 : 0] = sf;
-                } else if (f == 0) {
-                    S.phi[4 + r][c + 1] = sf;
-                } else if (f == 1) {
+                    S.phi[4 + r][lr ? kTileX + 3 : 0] = s1;
+                } else {
 #pragma unroll
                     for (int a = 0; a < 9; ++a) v[a] = sp[(9 + a) * P];
-                    S.phs[4 + r][c] = sum9(v) - (d.rhoA + sf * d.drho) * kCs2;
-                } else if (f == 2) {
-                    S.T[4 + r][c] = sf;
-                } else {
-                    S.psi[4 + r][c] = sf;
+                    const float s2 = sum9(v);
+                    if (f == 0) {
+                        S.phi[4 + r][c + 1] = s1;
+                        S.phs[4 + r][c] = s2 - (d.rhoA + s1 * d.drho) * kCs2;
+                    } else {
+                        S.T[4 + r][c] = s1;
+                        S.psi[4 + r][c] = s2;
+                        S.sig[4 + r][c] = sigma_eos(d, s1, s2);
+                    }
                 }
             }
         }
@@ -1217,24 +1221,25 @@ __device__ __forceinline__ void stream_strip(const LbmDev& d, float* __restrict_
                 if (c >= 1 && c <= kTileX + 2) {
                     S.phs[j][c - 1] = S.phs[js][c - 1];
                     S.psi[j][c - 1] = S.psi[js][c - 1];
-                    S.T[j][c - 1] = 2.0f * (y < 1 ? d.T_H : d.T_C) - S.T[js][c - 1];
+                    const float Tm = 2.0f * (y < 1 ? d.T_H : d.T_C) - S.T[js][c - 1];
+                    S.T[j][c - 1] = Tm;
+                    S.sig[j][c - 1] = sigma_eos(d, Tm, S.psi[js][c - 1]);
                 }
             }
             __syncthreads();
         }
         if (k >= c0) {
-            // normals and sigma on window rows 1..10; rows 1 and 2 were rows
-            // 9 and 10 of the previous iteration (rolled), unless this is the
-            // strip's first update or the window reaches a wall
+            // normals on window rows 1..10; rows 1 and 2 were rows 9 and 10
+            // of the previous iteration (rolled), unless this is the strip's
+            // first update or the window reaches a wall
             const int j0 = (k == c0 || walled) ? 1 : 3;
             for (int i = tid + (j0 - 1) * (kTileX + 2); i < (kWin - 2) * (kTileX + 2); i += NT) {
                 const int jr = i / (kTileX + 2), c = i % (kTileX + 2);
                 float gxp, gyp;
                 grad_smem<kTileX + 4>(S.phi, jr + 1, c + 1, gxp, gyp);
-                const float inv = 1.0f / fmaxf(sqrtf(gxp * gxp + gyp * gyp), kNormalEps);
+                const float inv = fminf(rsqrtf(gxp * gxp + gyp * gyp), 1.0f / kNormalEps);
                 S.nrmx[jr][c] = gxp * inv;
                 S.nrmy[jr][c] = gyp * inv;
-                S.sig[jr + 1][c] = sigma_eos(d, S.T[jr + 1][c], S.psi[jr + 1][c]);
             }
             __syncthreads();
             // update window row ty + 2: the carry (ty < 2) or chunk row ty - 2
@@ -1258,42 +1263,32 @@ __device__ __forceinline__ void stream_strip(const LbmDev& d, float* __restrict_
             }
         }
         // the window rolls by 8 rows: rows 8..11 -> 0..3 (fields), 9..10 ->
-        // 1..2 (normals, sigma)
+        // 1..2 (normals)
         {
             constexpr int W4 = kTileX + 4, W2 = kTileX + 2;
             constexpr int n4 = 4 * W4 / 4, n2 = 4 * W2 / 4, m2 = 2 * W2 / 4;
             static_assert((4 * W4) % 4 == 0 && (4 * W2) % 4 == 0 && (2 * W2) % 4 == 0,
                           "whole float4 rows");
-            for (int i = tid; i < n4 + 3 * n2 + 3 * m2; i += NT) {
+            for (int i = tid; i < n4 + 4 * n2 + 2 * m2; i += NT) {
                 if (i < n4) {
                     reinterpret_cast<float4*>(&S.phi[0][0])[i] =
                         reinterpret_cast<const float4*>(&S.phi[kTileY][0])[i];
                     continue;
                 }
                 int q = i - n4;
-                if (q < 3 * n2) {
-                    float(*arr)[W2] = q < n2 ? S.phs : (q < 2 * n2 ? S.T : S.psi);
+                if (q < 4 * n2) {
+                    const int w = q / n2;
+                    float(*arr)[W2] = w == 0 ? S.phs : (w == 1 ? S.T : (w == 2 ? S.psi : S.sig));
                     q %= n2;
                     reinterpret_cast<float4*>(&arr[0][0])[q] =
                         reinterpret_cast<const float4*>(&arr[kTileY][0])[q];
                     continue;
                 }
-                q -= 3 * n2;
-                const int w = q / m2;
+                q -= 4 * n2;
+                float(*arr)[W2] = q < m2 ? S.nrmx : S.nrmy;
                 q %= m2;
-                if (w == 0) {
-                    // sig rows 1 and 9 start 8 bytes past a 16-byte boundary
-                    reinterpret_cast<float2*>(&S.sig[1][0])[2 * q] =
-                        reinterpret_cast<const float2*>(&S.sig[kTileY + 1][0])[2 * q];
-                    reinterpret_cast<float2*>(&S.sig[1][0])[2 * q + 1] =
-                        reinterpret_cast<const float2*>(&S.sig[kTileY + 1][0])[2 * q + 1];
-                } else if (w == 1) {
-                    reinterpret_cast<float4*>(&S.nrmx[0][0])[q] =
-                        reinterpret_cast<const float4*>(&S.nrmx[kTileY][0])[q];
-                } else {
-                    reinterpret_cast<float4*>(&S.nrmy[0][0])[q] =
-                        reinterpret_cast<const float4*>(&S.nrmy[kTileY][0])[q];
-                }
+                reinterpret_cast<float4*>(&arr[0][0])[q] =
+                    reinterpret_cast<const float4*>(&arr[kTileY][0])[q];
             }
         }
         __syncthreads();
