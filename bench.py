@@ -302,6 +302,11 @@ def run_gpu(args) -> None:
         barrier()
         return ev0.elapsed_time(ev1), sum(s.launches() for s in sims) - l0
 
+    # measured strip plan of the batched launch (steps outside the timed region)
+    tuned_steps = 0
+    if args.mode == "batched" and args.tune_steps > 0:
+        tuned_steps = lbm.lbm_tune_batch(sims, args.tune_steps)
+    plan = lbm.lbm_batch_plan(sims)
     for _ in range(args.warmup):
         step_all()
     with ClockSampler(dev_index) as clk:
@@ -350,6 +355,8 @@ def run_gpu(args) -> None:
                        "sims_per_gpu": len(params), "fluid_nodes_per_step": nodes_per_step,
                        "launch_mode": args.mode + (" graph" if args.graph and args.mode == "plain" else ""),
                        "other_mode": other,
+                       "strip_plan": {"tuned": tuned_steps > 0, "tuning_steps": tuned_steps,
+                                      "strip_chunks": sorted(set(plan) - {0})},
                        "storage": args.precision,
                        "l2": "working set %.0f MB > 129 MB L2; simulations interleaved per step"
                              % (sum(2 * BYTES_PER_NODE_BUFFER[args.precision] * p["nx"] * p["ny"]
@@ -454,6 +461,9 @@ def main():
                     help="plain mode: advance each simulation by all timed steps in one "
                          "lbm_step call (replayed CUDA graphs of 64 steps)")
     ap.add_argument("--compare-modes", action="store_true", default=True)
+    ap.add_argument("--tune-steps", type=int, default=10,
+                    help="batched mode: steps per candidate strip plan for lbm_tune_batch "
+                         "before the warm-up (0: the cost model's plan)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

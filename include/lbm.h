@@ -179,6 +179,32 @@ lbm_status lbm_step(lbm_sim* sim, int64_t nsteps);
  * LBM_ESTATE, LBM_ECUDA. */
 lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps);
 
+/* Strip plan of a batch.  FP32 sims with walls, nx a multiple of 32 and at
+ * least 16 fluid rows are stepped by the streaming kernel: one block walks a
+ * 32-wide column over a strip of chunks of 8 rows.  strip_chunks[i] (caller's
+ * array of n) receives the strip length, in chunks, that lbm_step_batch uses
+ * for sims[i] in this batch (0 for sims stepped by the tile kernel).  Without
+ * tuning it comes from a cost model of the launch (one strip per block slot,
+ * 2 x SMs slots, longest first).  Host only; arguments as lbm_step_batch.  The
+ * paper has no counterpart (it fixes no GPU work decomposition).  Errors:
+ * LBM_EINVAL, LBM_ESTATE. */
+lbm_status lbm_batch_plan(lbm_sim* const* sims, int32_t n, int32_t* strip_chunks);
+
+/* Measured choice of the strip plan of a batch (autotuner).  For each
+ * distinct plan among the candidate strip lengths (the cost model's first),
+ * advances the whole batch trial_steps steps and times them with CUDA events
+ * on the batch's stream; the fastest plan is kept and used by later
+ * lbm_step_batch calls on sims of the same sizes in the same order, on this
+ * host thread (a plan cache of 16 size lists; tuned plans are evicted last).
+ * The trial steps are real steps: a step's result does not depend on the
+ * plan, so every sim advances *steps_taken steps (1 untimed warm-up step +
+ * trial_steps per candidate), as if by lbm_step_batch.  A batch with no
+ * streaming sim takes no step.  Synchronises the stream.  The paper has no
+ * counterpart.  Errors: LBM_EINVAL (trial_steps < 1, steps_taken NULL, batch
+ * arguments), LBM_ESTATE, LBM_ECUDA. */
+lbm_status lbm_tune_batch(lbm_sim* const* sims, int32_t n, int32_t trial_steps,
+                          int64_t* steps_taken);
+
 /* Computes the observables of the current state (out may be NULL) and, if
  * host_fields != NULL, copies the macroscopic fields phi, u_x, u_y, p, T, psi
  * into the host double array [6][ny][nx] (wall rows set to 0).  Synchronises

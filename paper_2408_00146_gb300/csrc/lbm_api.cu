@@ -261,80 +261,134 @@ bool encode_population_maps(lbm_sim* s)
 
 const CUtensorMap* map_of(const lbm_sim* s, int buf) { return s->have_tmap ? &s->tmap[buf] : nullptr; }
 
-// Strip lengths for one streaming launch over n lattices.  A strip of L
-// chunks costs about L + 2 chunk-times (the chunk below it is read first,
-// plus start-up); strips run on 2 x num_sms block slots in launch order,
-// longest first.  For each candidate target length the strips are placed by
-// that rule (a slot takes the next strip when it frees) and the candidate
-// with the shortest predicted launch wins; a lattice with fewer chunks than
-// the target takes whole columns.  The prediction is cached for the last
-// few size lists, since lbm_step_batch may be called once per step.
-void plan_strips(const LbmDev* const* devs, int n, int num_sms, int* out)
+// Strip lengths for one streaming launch over n lattices (plan[i]: chunks of
+// 8 rows per strip of lattice i).  The candidates are target lengths L; a
+// lattice with nch chunks per column is cut into ceil(nch / L) strips of
+// equal length (at least 4 chunks), so one with fewer chunks than L takes
+// whole columns.
+std::vector<int> candidate_lengths(int maxch)
 {
-    struct Entry {
-        int n = -1, sms = 0;
-        int nchunks[kMaxBatch], ncol[kMaxBatch], plan[kMaxBatch];
-    };
-    static thread_local Entry cache[8];
-    static thread_local int next = 0;
-    int nch[kMaxBatch], ncol[kMaxBatch], maxch = 1;
+    std::vector<int> cand = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+    for (int k = 1; k <= 16; ++k) cand.push_back((maxch + k - 1) / k);
+    std::vector<int> out;
+    for (int L : cand)
+        if (L >= 4 && L <= std::max(maxch, 4) && std::find(out.begin(), out.end(), L) == out.end())
+            out.push_back(L);
+    return out;
+}
+
+void plan_for_length(const int* nch, int n, int L, int* plan)
+{
+    for (int i = 0; i < n; ++i) {
+        const int ns = (nch[i] + L - 1) / L;
+        plan[i] = std::max(4, (nch[i] + ns - 1) / ns);
+    }
+}
+
+// The model: a strip of L chunks costs about L + 2 chunk-times (the chunk
+// below it is read first, plus start-up); strips run on 2 x num_sms block
+// slots in launch order, longest first, a slot taking the next strip when it
+// frees.  Returns the predicted launch time in chunk-times.
+double predicted_span(const int* nch, const int* ncol, int n, const int* plan, int slots)
+{
+    std::vector<int> lens;
+    for (int i = 0; i < n; ++i) {
+        const int per_col = (nch[i] + plan[i] - 1) / plan[i];
+        for (int c = 0; c < ncol[i]; ++c)
+            for (int t = 0; t < per_col; ++t) lens.push_back(std::min(plan[i], nch[i] - t * plan[i]));
+    }
+    std::sort(lens.begin(), lens.end(), std::greater<int>());
+    std::vector<double> load(slots, 0.0);
+    std::make_heap(load.begin(), load.end(), std::greater<double>());
+    double span = 0.0;
+    for (int l : lens) {
+        std::pop_heap(load.begin(), load.end(), std::greater<double>());
+        load.back() += l + 2.0;
+        span = std::max(span, load.back());
+        std::push_heap(load.begin(), load.end(), std::greater<double>());
+    }
+    return span;
+}
+
+// Plans by list of lattice sizes (chunks and columns, in launch-group
+// order), since lbm_step_batch may be called once per step.  A plan measured
+// by lbm_tune_batch (tuned) replaces the model's and is evicted last.
+struct PlanEntry {
+    int n = -1, sms = 0;
+    bool tuned = false;
+    int nchunks[kMaxBatch], ncol[kMaxBatch], plan[kMaxBatch];
+};
+constexpr int kPlanCache = 16;
+thread_local PlanEntry plan_cache[kPlanCache];
+thread_local int plan_next = 0;
+
+void plan_key(const LbmDev* const* devs, int n, int* nch, int* ncol)
+{
     for (int i = 0; i < n; ++i) {
         nch[i] = (devs[i]->nfy + kTileY - 1) / kTileY;
         ncol[i] = stream_columns(*devs[i]);
-        maxch = std::max(maxch, nch[i]);
     }
-    for (Entry& e : cache) {
-        if (e.n != n || e.sms != num_sms) continue;
+}
+
+PlanEntry* find_plan(const int* nch, const int* ncol, int n, int sms)
+{
+    for (PlanEntry& e : plan_cache) {
+        if (e.n != n || e.sms != sms) continue;
         bool same = true;
         for (int i = 0; i < n && same; ++i) same = e.nchunks[i] == nch[i] && e.ncol[i] == ncol[i];
-        if (same) {
-            std::memcpy(out, e.plan, sizeof(int) * n);
-            return;
+        if (same) return &e;
+    }
+    return nullptr;
+}
+
+void store_plan(const int* nch, const int* ncol, int n, int sms, const int* plan, bool tuned)
+{
+    PlanEntry* e = find_plan(nch, ncol, n, sms);
+    if (!e) {
+        // round robin, passing over tuned entries while an untuned one is left
+        for (int k = 0; k < kPlanCache && !e; ++k) {
+            PlanEntry& c = plan_cache[(plan_next + k) % kPlanCache];
+            if (!c.tuned) {
+                e = &c;
+                plan_next = (plan_next + k + 1) % kPlanCache;
+            }
+        }
+        if (!e) {
+            e = &plan_cache[plan_next];
+            plan_next = (plan_next + 1) % kPlanCache;
         }
     }
+    e->n = n;
+    e->sms = sms;
+    e->tuned = tuned;
+    std::memcpy(e->nchunks, nch, sizeof(int) * n);
+    std::memcpy(e->ncol, ncol, sizeof(int) * n);
+    std::memcpy(e->plan, plan, sizeof(int) * n);
+}
+
+// The plan lbm_step_batch uses: a cached one (tuned or predicted), else the
+// candidate with the shortest predicted launch.
+void plan_strips(const LbmDev* const* devs, int n, int num_sms, int* out)
+{
+    int nch[kMaxBatch], ncol[kMaxBatch];
+    plan_key(devs, n, nch, ncol);
+    if (const PlanEntry* e = find_plan(nch, ncol, n, num_sms)) {
+        std::memcpy(out, e->plan, sizeof(int) * n);
+        return;
+    }
+    const int maxch = std::max(1, *std::max_element(nch, nch + n));
     const int slots = 2 * std::max(num_sms, 1);
-    std::vector<int> cand = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
-    for (int k = 1; k <= 16; ++k) cand.push_back((maxch + k - 1) / k);
     double best = 1e300;
-    int best_plan[kMaxBatch];
-    std::vector<int> lens;
-    std::vector<double> load;
-    for (int L : cand) {
-        if (L < 4 || L > maxch) continue;
-        int plan[kMaxBatch];
-        lens.clear();
-        for (int i = 0; i < n; ++i) {
-            const int ns = (nch[i] + L - 1) / L;
-            plan[i] = std::max(4, (nch[i] + ns - 1) / ns);
-            const int per_col = (nch[i] + plan[i] - 1) / plan[i];
-            for (int c = 0; c < ncol[i]; ++c)
-                for (int t = 0; t < per_col; ++t)
-                    lens.push_back(std::min(plan[i], nch[i] - t * plan[i]));
-        }
-        std::sort(lens.begin(), lens.end(), std::greater<int>());
-        load.assign(slots, 0.0);
-        std::make_heap(load.begin(), load.end(), std::greater<double>());
-        double span = 0.0;
-        for (int l : lens) {
-            std::pop_heap(load.begin(), load.end(), std::greater<double>());
-            load.back() += l + 2.0;
-            span = std::max(span, load.back());
-            std::push_heap(load.begin(), load.end(), std::greater<double>());
-        }
+    int best_plan[kMaxBatch], plan[kMaxBatch];
+    for (int L : candidate_lengths(maxch)) {
+        plan_for_length(nch, n, L, plan);
+        const double span = predicted_span(nch, ncol, n, plan, slots);
         if (span < best - 1e-9) {
             best = span;
             std::memcpy(best_plan, plan, sizeof(int) * n);
         }
     }
-    if (best == 1e300)
-        for (int i = 0; i < n; ++i) best_plan[i] = std::max(4, nch[i]);
-    Entry& e = cache[next];
-    next = (next + 1) % 8;
-    e.n = n;
-    e.sms = num_sms;
-    std::memcpy(e.nchunks, nch, sizeof(int) * n);
-    std::memcpy(e.ncol, ncol, sizeof(int) * n);
-    std::memcpy(e.plan, best_plan, sizeof(int) * n);
+    store_plan(nch, ncol, n, num_sms, best_plan, false);
     std::memcpy(out, best_plan, sizeof(int) * n);
 }
 
@@ -662,11 +716,14 @@ lbm_status lbm_step(lbm_sim* s, int64_t nsteps)
     return LBM_OK;
 }
 
-lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
+}  // extern "C"
+
+// Arguments of a batch call: 1..kMaxBatch distinct initialised sims on one
+// stream and device.
+static lbm_status check_batch(lbm_sim* const* sims, int32_t n, const char* who)
 {
     if (!sims || n < 1 || n > kMaxBatch)
-        return fail(LBM_EINVAL, "lbm_step_batch needs 1..%d sims (got %d)", kMaxBatch, n);
-    if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+        return fail(LBM_EINVAL, "%s needs 1..%d sims (got %d)", who, kMaxBatch, n);
     long long total = 0;
     for (int i = 0; i < n; ++i) {
         const lbm_sim* s = sims[i];
@@ -679,6 +736,28 @@ lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
         total += tiles_of(s->dev);
     }
     if (total > 0x7fffffffLL) return fail(LBM_EINVAL, "too many tiles in one batch");
+    return LBM_OK;
+}
+
+// The streaming sims of a batch, in argument order, and their planned strip
+// lengths (plan[k] for stream[k]).
+static int stream_group(lbm_sim* const* sims, int n, lbm_sim** stream, int* plan)
+{
+    int sn = 0;
+    for (int i = 0; i < n; ++i)
+        if (sims[i]->ystream) stream[sn++] = sims[i];
+    if (sn > 0) {
+        const LbmDev* devs[kMaxBatch];
+        for (int i = 0; i < sn; ++i) devs[i] = &stream[i]->dev;
+        plan_strips(devs, sn, stream[0]->num_sms, plan);
+    }
+    return sn;
+}
+
+// nsteps batched steps; forced (optional) replaces the planned strip lengths
+// of the streaming group (one per streaming sim, in argument order).
+static lbm_status step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps, const int* forced)
+{
     // one launch per kernel family present: the streaming kernel for the
     // FP32 sims it takes, the tile kernel per storage precision for the rest
     static thread_local BatchArgs args[3];  // 20 KB each: kept off the stack
@@ -686,16 +765,15 @@ lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
     int tiles[3] = {0, 0, 0};
     lbm_sim* group[3][kMaxBatch];
     lbm_sim* sgroup[kMaxBatch];
-    int sn = 0;
     for (int k = 0; k < 3; ++k) {
         args[k].n = 0;
         args[k].first[0] = 0;
     }
+    int schunks[kMaxBatch];
+    const int sn = stream_group(sims, n, sgroup, schunks);
+    if (forced) std::memcpy(schunks, forced, sizeof(int) * sn);
     for (int i = 0; i < n; ++i) {
-        if (sims[i]->ystream) {
-            sgroup[sn++] = sims[i];
-            continue;
-        }
+        if (sims[i]->ystream) continue;
         const int k = sims[i]->p.precision;
         BatchArgs& a = args[k];
         group[k][a.n] = sims[i];
@@ -704,12 +782,6 @@ lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
         a.first[a.n + 1] = a.first[a.n] + tiles_of(sims[i]->dev);
         tiles[k] = a.first[a.n + 1];
         a.n += 1;
-    }
-    int schunks[kMaxBatch];
-    if (sn > 0) {
-        const LbmDev* devs[kMaxBatch];
-        for (int i = 0; i < sn; ++i) devs[i] = &sgroup[i]->dev;
-        plan_strips(devs, sn, sgroup[0]->num_sms, schunks);
     }
     // longest strips first: blocks start in index order, so the short ones
     // fill the tail of the launch
@@ -749,6 +821,83 @@ lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
             sims[i]->t += 1;
         }
     }
+    return LBM_OK;
+}
+
+extern "C" {
+
+lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps)
+{
+    lbm_status st = check_batch(sims, n, "lbm_step_batch");
+    if (st != LBM_OK) return st;
+    if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+    return step_batch(sims, n, nsteps, nullptr);
+}
+
+lbm_status lbm_batch_plan(lbm_sim* const* sims, int32_t n, int32_t* strip_chunks)
+{
+    if (!strip_chunks) return fail(LBM_EINVAL, "strip_chunks is NULL");
+    lbm_status st = check_batch(sims, n, "lbm_batch_plan");
+    if (st != LBM_OK) return st;
+    lbm_sim* sg[kMaxBatch];
+    int plan[kMaxBatch];
+    stream_group(sims, n, sg, plan);
+    for (int i = 0, k = 0; i < n; ++i) strip_chunks[i] = sims[i]->ystream ? plan[k++] : 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_tune_batch(lbm_sim* const* sims, int32_t n, int32_t trial_steps, int64_t* steps_taken)
+{
+    if (!steps_taken) return fail(LBM_EINVAL, "steps_taken is NULL");
+    *steps_taken = 0;
+    lbm_status st = check_batch(sims, n, "lbm_tune_batch");
+    if (st != LBM_OK) return st;
+    if (trial_steps < 1) return fail(LBM_EINVAL, "trial_steps must be >= 1 (got %d)", trial_steps);
+    lbm_sim* sg[kMaxBatch];
+    int model[kMaxBatch];
+    const int sn = stream_group(sims, n, sg, model);
+    if (sn == 0) return LBM_OK;            // no streaming lattice: nothing to plan
+    int nch[kMaxBatch], ncol[kMaxBatch];
+    const LbmDev* devs[kMaxBatch];
+    for (int i = 0; i < sn; ++i) devs[i] = &sg[i]->dev;
+    plan_key(devs, sn, nch, ncol);
+    // distinct plans of the candidate lengths, the model's first
+    std::vector<std::vector<int>> plans{std::vector<int>(model, model + sn)};
+    std::vector<int> plan(sn);
+    for (int L : candidate_lengths(*std::max_element(nch, nch + sn))) {
+        plan_for_length(nch, sn, L, plan.data());
+        if (std::find(plans.begin(), plans.end(), plan) == plans.end()) plans.push_back(plan);
+    }
+    cudaSetDevice(sims[0]->device);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    // one untimed step first, so that the first candidate is not timed cold
+    if (e == cudaSuccess) st = step_batch(sims, n, 1, model);
+    int64_t steps = 1;
+    float best_ms = 0.0f;
+    size_t best = 0;
+    for (size_t c = 0; c < plans.size() && e == cudaSuccess && st == LBM_OK; ++c) {
+        e = cudaEventRecord(ev[0], sims[0]->stream);
+        if (e != cudaSuccess) break;
+        st = step_batch(sims, n, trial_steps, plans[c].data());
+        if (st != LBM_OK) break;
+        steps += trial_steps;
+        e = cudaEventRecord(ev[1], sims[0]->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    *steps_taken = steps;
+    if (st != LBM_OK) return st;
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "lbm_tune_batch: %s", cudaGetErrorString(e));
+    store_plan(nch, ncol, sn, sg[0]->num_sms, plans[best].data(), true);
     return LBM_OK;
 }
 

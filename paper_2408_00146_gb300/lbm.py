@@ -54,7 +54,7 @@ STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA"
 # Symbols include/lbm.h declares.
 EXPORTS = [
     "lbm_derive", "lbm_workspace_bytes", "lbm_create", "lbm_create_ex", "lbm_init", "lbm_step",
-    "lbm_step_batch",
+    "lbm_step_batch", "lbm_batch_plan", "lbm_tune_batch",
     "lbm_observe", "lbm_get_populations", "lbm_get_derived", "lbm_launch_count",
     "lbm_destroy", "lbm_last_error", "lbm_reduce_observables_noalloc", "lbm_probe_bounded_wait",
 ]
@@ -98,6 +98,10 @@ def load() -> ctypes.CDLL:
             L.lbm_init.argtypes = [vp, dp, fp]
             L.lbm_step.argtypes = [vp, ctypes.c_int64]
             L.lbm_step_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_int64]
+            L.lbm_batch_plan.argtypes = [ctypes.POINTER(vp), ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int32)]
+            L.lbm_tune_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int64)]
             L.lbm_observe.argtypes = [vp, ctypes.POINTER(LbmObs), dp]
             L.lbm_get_populations.argtypes = [vp, fp]
             L.lbm_get_derived.argtypes = [vp, dp]
@@ -185,12 +189,34 @@ def lbm_step(sim, nsteps: int):
     _check(load().lbm_step(sim, int(nsteps)), "lbm_step")
 
 
+def _handles(sims):
+    hs = [s.handle if isinstance(s, Sim) else s for s in sims]
+    return (ctypes.c_void_p * len(hs))(*[h.value if isinstance(h, ctypes.c_void_p) else h
+                                         for h in hs]), len(hs)
+
+
 def lbm_step_batch(sims, nsteps: int):
     """One launch per step over every simulation in `sims` (handles or Sim)."""
-    hs = [s.handle if isinstance(s, Sim) else s for s in sims]
-    arr = (ctypes.c_void_p * len(hs))(*[h.value if isinstance(h, ctypes.c_void_p) else h
-                                        for h in hs])
-    _check(load().lbm_step_batch(arr, len(hs), int(nsteps)), "lbm_step_batch")
+    arr, n = _handles(sims)
+    _check(load().lbm_step_batch(arr, n, int(nsteps)), "lbm_step_batch")
+
+
+def lbm_batch_plan(sims) -> list[int]:
+    """Strip length (chunks of 8 rows) lbm_step_batch uses for each sim; 0
+    for sims stepped by the tile kernel."""
+    arr, n = _handles(sims)
+    out = (ctypes.c_int32 * n)()
+    _check(load().lbm_batch_plan(arr, n, out), "lbm_batch_plan")
+    return list(out)
+
+
+def lbm_tune_batch(sims, trial_steps: int) -> int:
+    """Times every candidate strip plan on the batch for trial_steps steps and
+    keeps the fastest; returns the number of steps every sim advanced."""
+    arr, n = _handles(sims)
+    taken = ctypes.c_int64(0)
+    _check(load().lbm_tune_batch(arr, n, int(trial_steps), ctypes.byref(taken)), "lbm_tune_batch")
+    return int(taken.value)
 
 
 def lbm_observe(sim, host_fields: np.ndarray | None = None, check: bool = True) -> dict:
