@@ -367,7 +367,13 @@ void store_plan(const int* nch, const int* ncol, int n, int sms, const int* plan
 }
 
 // The plan lbm_step_batch uses: a cached one (tuned or predicted), else the
-// candidate with the shortest predicted launch.
+// candidate with the shortest predicted launch.  When even one strip per
+// column needs more than one wave of block slots, only strips of at most 16
+// chunks are considered: measured on the 64-channel ensemble, longer strips
+// in a multi-wave launch lose more to L2 misses of the side boxes (their
+// neighbouring columns run at other times) than they save in start-up.
+constexpr int kMultiWaveMaxStrip = 16;
+
 void plan_strips(const LbmDev* const* devs, int n, int num_sms, int* out)
 {
     int nch[kMaxBatch], ncol[kMaxBatch];
@@ -378,9 +384,13 @@ void plan_strips(const LbmDev* const* devs, int n, int num_sms, int* out)
     }
     const int maxch = std::max(1, *std::max_element(nch, nch + n));
     const int slots = 2 * std::max(num_sms, 1);
+    long long cols = 0;
+    for (int i = 0; i < n; ++i) cols += ncol[i];
+    const bool multi_wave = cols > slots;
     double best = 1e300;
     int best_plan[kMaxBatch], plan[kMaxBatch];
     for (int L : candidate_lengths(maxch)) {
+        if (multi_wave && L > kMultiWaveMaxStrip) continue;
         plan_for_length(nch, n, L, plan);
         const double span = predicted_span(nch, ncol, n, plan, slots);
         if (span < best - 1e-9) {
