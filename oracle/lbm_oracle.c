@@ -41,6 +41,13 @@
  *       T_w) for h; stencil ghosts at and beyond the walls are the mirror
  *       images about the wall plane (even for phi, psi, p*, odd about T_w
  *       for T).
+ *   R13 surfactant held at psi_L (y = 0 end) and psi_R (y = ny-1 end), the
+ *       paper's setting of its main cases (Sec. 2, Sec. 6): q takes the
+ *       anti-bounce-back Dirichlet rule of h with psi_w, and psi's stencil
+ *       ghosts are odd about psi_w, as T's about T_w (psi_bc = 1).  The
+ *       alternative at the end of Sec. 6 keeps zero-flux walls and uses
+ *       psi_L, psi_R only for the initial linear profile (psi_bc = 2), which
+ *       the input generators build.
  *   R11 L in U_o (Eq. (21)) is the lattice length ny along the temperature
  *       gradient.
  *   R12 n = grad phi / max(|grad phi|, 1e-4): the paper leaves n undefined
@@ -268,6 +275,9 @@ int orc_derive(const orc_params* p, orc_derived* d)
 {
     memset(d, 0, sizeof *d);
     if (p->nx < 4 || p->ny < (p->walls ? 5 : 4)) return -1;
+    if (p->psi_bc < 0 || p->psi_bc > 2 || !(p->psi_L >= 0.0 && p->psi_L < 1.0) ||
+        !(p->psi_R >= 0.0 && p->psi_R < 1.0))
+        return -1;
     if (!(p->rho_A > 0) || !(p->rho_ratio > 0) || !(p->mu_ratio > 0) ||
         !(p->alpha_ratio > 0) || !(p->W > 0) || !(p->T_ref != 0))
         return -1;
@@ -382,6 +392,17 @@ static double T_at(const orc_sim* s, int x, int y)
     return v;
 }
 
+/* psi at (x, y) with the wall ghosts of R10 / R13. */
+static double psi_at(const orc_sim* s, int x, int y)
+{
+    int side;
+    int r = src_row(s, y, &side);
+    double v = s->psi[(size_t)r * s->nx + wrapx(s, x)];
+    if (s->p.psi_bc == 1 && side < 0) return 2.0 * s->p.psi_L - v;
+    if (s->p.psi_bc == 1 && side > 0) return 2.0 * s->p.psi_R - v;
+    return v;
+}
+
 static double rho_of(const orc_sim* s, double phi)
 {
     return s->d.rho_A + phi * (s->d.rho_B - s->d.rho_A); /* Eq. (17), R2 */
@@ -399,7 +420,7 @@ static double alpha_of(const orc_sim* s, double phi)
 
 static double sigma_at(const orc_sim* s, int x, int y)
 {
-    return orc_sigma_eos(&s->p, T_at(s, x, y), even_at(s, s->psi, x, y));
+    return orc_sigma_eos(&s->p, T_at(s, x, y), psi_at(s, x, y));
 }
 
 static double phistar_at(const orc_sim* s, int x, int y)
@@ -715,7 +736,8 @@ static void collide(orc_sim* s)
 /* Streaming f_a(x, t+1) = f~_a(x - e_a) (Eqs. in App. B-E), periodic in x
  * (and in y without walls); a population whose source is a wall node is the
  * one that left this node towards the wall, reversed (halfway bounce-back,
- * R10), for h with the anti-bounce-back Dirichlet term 2 w_a T_w. */
+ * R10), for h with the anti-bounce-back Dirichlet term 2 w_a T_w, and for q
+ * with 2 w_a psi_w when psi is held at the walls (R13). */
 static void stream(orc_sim* s)
 {
     const int nx = s->nx, ny = s->ny;
@@ -736,7 +758,12 @@ static void stream(orc_sim* s)
                     POP(s, 0, a, i) = POST(s, 0, OPP[a], i);
                     POP(s, 1, a, i) = POST(s, 1, OPP[a], i);
                     POP(s, 2, a, i) = -POST(s, 2, OPP[a], i) + 2.0 * WGT[a] * Tw;
-                    POP(s, 3, a, i) = POST(s, 3, OPP[a], i);
+                    if (s->p.psi_bc == 1) {
+                        double psiw = (sy <= 0) ? s->p.psi_L : s->p.psi_R;
+                        POP(s, 3, a, i) = -POST(s, 3, OPP[a], i) + 2.0 * WGT[a] * psiw;
+                    } else {
+                        POP(s, 3, a, i) = POST(s, 3, OPP[a], i);
+                    }
                 }
             }
         }

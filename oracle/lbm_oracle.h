@@ -53,6 +53,11 @@ typedef struct {
     double gravity;      /* buoyancy -(rho-rho_A) g along y (Sec. 5.3)      */
     double nu_A;         /* > 0: ambient kinematic viscosity given directly */
     double alpha_A;      /* > 0: ambient thermal diffusivity given directly */
+    double psi_L, psi_R; /* surfactant at the y=0 and y=ny-1 ends (Sec. 2, 6) */
+    int32_t psi_bc;      /* 0: zero-flux walls; 1: psi fixed to psi_L, psi_R
+                            at the wall planes (Sec. 6 main cases); 2: zero
+                            flux with psi_L, psi_R only as the initial
+                            profile (the variant at the end of Sec. 6)      */
 } orc_params;
 
 /* Lattice parameters derived from orc_params (Step P). */

@@ -36,7 +36,10 @@ PARAM_FIELDS = [
     ("Fext_x", ctypes.c_double), ("Fext_y", ctypes.c_double),
     ("gravity", ctypes.c_double), ("nu_A", ctypes.c_double),
     ("alpha_A", ctypes.c_double),
+    ("psi_L", ctypes.c_double), ("psi_R", ctypes.c_double), ("psi_bc", ctypes.c_int32),
 ]
+# parameters added after the first release: absent from a dict means 0
+OPTIONAL = ("psi_L", "psi_R", "psi_bc")
 
 DERIVED_FIELDS = [
     "dT", "M1", "M2", "L", "U_o", "rho_A", "rho_B", "mu_A", "mu_B", "nu_A",
@@ -124,7 +127,7 @@ def _dp(a: np.ndarray):
 def make_params(d: dict) -> OrcParams:
     p = OrcParams()
     for name, _ in PARAM_FIELDS:
-        setattr(p, name, d[name])
+        setattr(p, name, d.get(name, 0) if name in OPTIONAL else d[name])
     return p
 
 

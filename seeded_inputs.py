@@ -24,7 +24,7 @@ PARAM_NAMES = (
     "nx", "ny", "walls", "R", "xb", "yb", "W", "M_phi", "rho_A", "rho_ratio",
     "mu_ratio", "alpha_ratio", "Re", "Ma", "sigma0", "sigma_T", "sigma_TT",
     "T_ref", "T_H", "T_C", "beta", "Pi", "Ex", "M_psi", "psi0", "Fext_x",
-    "Fext_y", "gravity", "nu_A", "alpha_A",
+    "Fext_y", "gravity", "nu_A", "alpha_A", "psi_L", "psi_R", "psi_bc",
 )
 
 # Bubble in a periodic-x channel with a hot wall at y=0 and a cold wall at
@@ -37,7 +37,7 @@ CHANNEL_64x128 = dict(
     rho_A=1.0, rho_ratio=10.0, mu_ratio=1.0, alpha_ratio=1.0, Re=1.0, Ma=10.0,
     sigma0=5e-3, sigma_T=0.0, sigma_TT=1e-3, T_ref=0.5, T_H=1.0, T_C=0.0,
     beta=0.1, Pi=8.33, Ex=0.16, M_psi=0.01, psi0=0.5, Fext_x=0.0, Fext_y=0.0,
-    gravity=0.0, nu_A=0.0, alpha_A=0.0,
+    gravity=0.0, nu_A=0.0, alpha_A=0.0, psi_L=0.0, psi_R=0.0, psi_bc=0,
 )
 
 # Gibbs elasticity x quadratic sensitivity sweep of the 256x1024 channel.
@@ -89,18 +89,28 @@ def linear_wall_temperature(p: dict) -> np.ndarray:
     return p["T_H"] + (p["T_C"] - p["T_H"]) * (y - 0.5) / (p["ny"] - 2.0)
 
 
+def initial_psi(p: dict) -> np.ndarray:
+    """psi0 everywhere, or, with psi_bc 1 or 2 and walls, psi_L on the wall
+    plane y=1/2 and psi_R on y=ny-3/2, linear in between (Sec. 2, Sec. 6)."""
+    _, y = _grid(p)
+    if not p["walls"] or p.get("psi_bc", 0) == 0:
+        return np.full((p["ny"], p["nx"]), float(p["psi0"]))
+    return p["psi_L"] + (p["psi_R"] - p["psi_L"]) * (y - 0.5) / (p["ny"] - 2.0)
+
+
 def bubble_fields(p: dict, seed: int | None = None, psi_noise: float = 0.0,
                   u_noise: float = 0.0, T_noise: float = 0.0,
                   p_noise: float = 0.0) -> np.ndarray:
     """Circular bubble (phi = 1 inside) of radius R at (xb, yb) with the
     hyperbolic-tangent interface profile, u = 0, p = 0, linear wall-to-wall T
-    and psi = psi0, plus optional seeded uniform noise on psi, u, T and p."""
+    and the initial psi of initial_psi, plus optional seeded uniform noise on
+    psi, u, T and p."""
     x, y = _grid(p)
     r = np.hypot(x - p["xb"], y - p["yb"])
     out = np.zeros((6, p["ny"], p["nx"]))
     out[0] = 0.5 + 0.5 * np.tanh(2.0 * (p["R"] - r) / p["W"]) if p["R"] > 0 else 0.0
     out[4] = linear_wall_temperature(p)
-    out[5] = p["psi0"]
+    out[5] = initial_psi(p)
     if seed is not None:
         rng = np.random.default_rng(seed)
         shape = (p["ny"], p["nx"])

@@ -152,6 +152,56 @@ def test_heat_conduction_between_walls(orc):
     assert np.abs(T - (1 - xi / H)).max() < 1e-6
 
 
+def test_surfactant_held_at_the_walls(orc):
+    """psi_bc = 1 (the paper's psi_L, psi_R ends, Sec. 6): with no interface
+    the q scheme is plain diffusion with Dirichlet walls, so from psi = 0 the
+    profile follows the Fourier series
+    psi = psi_L + (psi_R - psi_L) xi/H - sum 2/(n pi) (psi_L - psi_R (-1)^n)
+          sin(n pi xi/H) exp(-D (n pi/H)^2 t)
+    (xi from the y=0 wall plane, H = ny - 2, D = M_psi), then the linear
+    steady state; T is untouched by it."""
+    D, psL, psR = 0.05, 0.4, 0.1
+    p = _quiet(si.channel_64x128(), nx=4, ny=34, R=0.0, M_psi=D, psi_bc=1, psi_L=psL,
+               psi_R=psR, T_H=0.5, T_C=0.5)
+    o = orc.Oracle(p)
+    o.init_fields(si.uniform_fields(p, psi=0.0))
+    H = 32.0
+    xi = np.arange(1, 33) - 0.5
+    n = np.arange(1, 4000)[:, None]
+    for steps in (500, 1500):
+        o.step(steps - o.t)
+        F = o.fields()
+        ps = F[5, 1:33, 2]
+        pa = psL + (psR - psL) * xi / H - np.sum(
+            2 / (n * np.pi) * (psL - psR * (-1.0) ** n) * np.sin(n * np.pi * xi / H) *
+            np.exp(-D * (n * np.pi / H) ** 2 * o.t), axis=0)
+        assert np.abs(ps - pa).max() < 1e-3, steps
+        assert np.abs(F[4, 1:33]).max() == pytest.approx(0.5, abs=1e-12)
+        assert np.abs(F[1:3, 1:33]).max() < 1e-12
+    p.update(M_psi=0.3)
+    o = orc.Oracle(p)
+    o.init_fields(si.uniform_fields(p, psi=0.0))
+    o.step(8000)
+    ps = o.fields()[5, 1:33, 2]
+    assert np.abs(ps - (psL + (psR - psL) * xi / H)).max() < 1e-6
+
+
+def test_surfactant_initial_gradient_with_zero_flux_walls(orc):
+    """psi_bc = 2 (the variant at the end of Sec. 6): psi_L, psi_R set only the
+    initial linear profile; the walls pass no surfactant, so sum psi is
+    conserved and the profile relaxes to its mean (psi_L + psi_R)/2."""
+    p = _quiet(si.channel_64x128(), nx=4, ny=34, R=0.0, M_psi=0.3, psi_bc=2, psi_L=0.4,
+               psi_R=0.1, T_H=0.5, T_C=0.5)
+    f0 = si.bubble_fields(p)
+    assert f0[5, 1, 0] == pytest.approx(0.4 + (0.1 - 0.4) * 0.5 / 32)
+    o = orc.Oracle(p)
+    o.init_fields(f0)
+    m0 = o.observe()["mass_psi"]
+    o.step(8000)
+    assert o.observe()["mass_psi"] == pytest.approx(m0, rel=1e-12)
+    assert np.abs(o.fields()[5, 1:33] - 0.25).max() < 1e-6
+
+
 @pytest.mark.parametrize("psi_inf0", [0.05, 0.15, 0.225])
 def test_flat_interface_surfactant_equilibrium(orc, psi_inf0):
     """Sec. 5.2: W = 5, Ex = 0.025, Pi = 50, sigma0 = 0.01, M_phi = 0.02.  At
