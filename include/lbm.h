@@ -13,8 +13,9 @@
  * of Sec. 3.
  *
  * Geometry: x is periodic.  With walls != 0, rows y = 0 and y = ny-1 are solid
- * (halfway bounce-back for f, g, q; anti-bounce-back Dirichlet temperature
- * T_H at y = 0 and T_C at y = ny-1 for h) and rows 1..ny-2 are fluid; with
+ * (halfway bounce-back for f, g and, by default, q; anti-bounce-back Dirichlet
+ * temperature T_H at y = 0 and T_C at y = ny-1 for h, and for q when psi is
+ * held at psi_L / psi_R, see psi_bc) and rows 1..ny-2 are fluid; with
  * walls == 0, y is periodic too.  phi = 0 is the ambient fluid A, phi = 1
  * the bubble B (Sec. 3).
  *
@@ -94,6 +95,17 @@ typedef struct {
     double nu_A;           /* > 0: ambient kinematic viscosity given directly   */
     double alpha_A;        /* > 0: ambient thermal diffusivity given directly   */
     int32_t precision;     /* LBM_FP32, LBM_FP16 or LBM_BF16 (storage, above)   */
+    double psi_L, psi_R;   /* surfactant at the y=0 and y=ny-1 ends, in [0, 1)  */
+    int32_t psi_bc;        /* walls for psi (Sec. 2, Sec. 6): 0 zero flux (halfway
+                              bounce-back for q) and uniform initial psi0; 1 psi
+                              held at psi_L, psi_R on the wall planes (anti-
+                              bounce-back for q with 2 w_a psi_w, stencil ghosts
+                              odd about psi_w), the paper's main cases; 2 zero
+                              flux with psi_L -> psi_R only as the linear
+                              initial profile (the variant at the end of
+                              Sec. 6).  1 and 2 set the analytic initial psi
+                              linear between the wall planes.  Needs walls = 1
+                              to have an effect.                               */
 } lbm_params;
 
 /* Observables (Sec. 5.3, Sec. 6): phi-weighted bubble centroid ("mass

@@ -64,6 +64,9 @@ lbm_status derive(const lbm_params* p, double* out)
     if (!(p->rho_A > 0) || !(p->rho_ratio > 0) || !(p->mu_ratio > 0) || !(p->alpha_ratio > 0) ||
         !(p->W > 0) || !(p->T_ref != 0))
         return fail(LBM_EINVAL, "rho_A, rho_ratio, mu_ratio, alpha_ratio, W must be > 0, T_ref != 0");
+    if (p->psi_bc < 0 || p->psi_bc > 2) return fail(LBM_EINVAL, "psi_bc must be 0, 1 or 2");
+    if (!(p->psi_L >= 0.0 && p->psi_L < 1.0) || !(p->psi_R >= 0.0 && p->psi_R < 1.0))
+        return fail(LBM_EINVAL, "psi_L and psi_R must lie in [0, 1)");
     if (p->R > 0 && 2 * p->R >= (p->nx < p->ny ? p->nx : p->ny))
         return fail(LBM_EINVAL, "bubble radius %.3g does not fit the lattice", p->R);
     const double dT = p->T_H - p->T_C;
@@ -150,6 +153,9 @@ LbmDev make_dev(const lbm_params* p, const double* dv)
     d.xb = (float)p->xb;
     d.yb = (float)p->yb;
     d.psi0 = (float)p->psi0;
+    d.psi_L = (float)p->psi_L;
+    d.psi_R = (float)p->psi_R;
+    d.psi_bc = p->psi_bc;
     return d;
 }
 

@@ -32,6 +32,10 @@ struct LbmDev {
     float Fext_x, Fext_y, gravity;
     // analytic initial state
     float R, xb, yb, psi0;
+    // surfactant at the walls: psi_bc 0 zero flux, 1 held at psi_L (y=0) and
+    // psi_R (y=ny-1), 2 zero flux with the psi_L -> psi_R initial profile
+    float psi_L, psi_R;
+    int psi_bc;
 };
 
 // Tile shape of the fused step kernel.

@@ -62,6 +62,15 @@ __device__ __forceinline__ int src_row(const LbmDev& d, int y, int& side)
     return min(max(y, 1), d.ny - 2);
 }
 
+// Stencil ghost of psi at a wall mirror (side -1 below the y=0 wall, +1
+// above the y=ny-1 wall): even about the wall plane for zero-flux walls, odd
+// about psi_w when psi is held at psi_L / psi_R (psi_bc 1), as T about T_w.
+__device__ __forceinline__ float psi_ghost(const LbmDev& d, float psi, int side)
+{
+    if (d.psi_bc != 1 || side == 0) return psi;
+    return 2.0f * (side < 0 ? d.psi_L : d.psi_R) - psi;
+}
+
 // Surface tension law, Eq. (6); ln(1 - psi) with psi clamped to [0, 1-1e-6].
 __device__ __forceinline__ float sigma_eos(const LbmDev& d, float T, float psi)
 {
@@ -421,7 +430,7 @@ __device__ __forceinline__ NodeMoments own_moments(const LbmDev& d, const TileSm
     if (side < 0) Tg = 2.0f * d.T_H - m.T;
     if (side > 0) Tg = 2.0f * d.T_C - m.T;
     sm.phi[ty + 2][tx + 2] = m.phi;
-    sm.sig[ty + 1][tx + 1] = sigma_eos(d, Tg, m.psi);
+    sm.sig[ty + 1][tx + 1] = sigma_eos(d, Tg, psi_ghost(d, m.psi, side));
     sm.phs[ty + 1][tx + 1] = m.pst - (d.rhoA + m.phi * d.drho) * kCs2;
     return m;
 }
@@ -436,7 +445,7 @@ __device__ __forceinline__ void halo_fields(const LbmDev& d, const TileSmem& sm,
     if (ring1) {
         if (side < 0) Th = 2.0f * d.T_H - Th;
         if (side > 0) Th = 2.0f * d.T_C - Th;
-        sm.sig[ey - 1][ex - 1] = sigma_eos(d, Th, sp);
+        sm.sig[ey - 1][ex - 1] = sigma_eos(d, Th, psi_ghost(d, sp, side));
         sm.phs[ey - 1][ex - 1] = ps - (d.rhoA + ph * d.drho) * kCs2;
     }
 }
@@ -546,7 +555,10 @@ __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
         const float dG = (phi - 0.5f) * (d.g_s32 * phi * (1.0f - phi) + d.g_w);
         const float flux = -d.m_psi * psi * (1.0f - psi) * dG;   // times grad phi
         scalar_collide(v, psi, flux * gpx, flux * gpy, d.omega_psi, ux, uy);
-        Mq = st.template put<false>(3, N, nb, v, psi, wall, 0.0f);
+        // walls: halfway bounce-back, or anti-bounce-back with psi_L / psi_R
+        Mq = d.psi_bc == 1
+                 ? st.template put<true>(3, N, nb, v, psi, wall, wall < 0 ? d.psi_L : d.psi_R)
+                 : st.template put<false>(3, N, nb, v, psi, wall, 0.0f);
     }
     // ---- g: two-fluid pressure/velocity (App. C) ----------------------------------------
     {
@@ -1220,10 +1232,11 @@ __device__ __forceinline__ void stream_strip(const LbmDev& d, float* __restrict_
                 S.phi[j][c] = S.phi[js][c];
                 if (c >= 1 && c <= kTileX + 2) {
                     S.phs[j][c - 1] = S.phs[js][c - 1];
-                    S.psi[j][c - 1] = S.psi[js][c - 1];
+                    const float pm = psi_ghost(d, S.psi[js][c - 1], y < 1 ? -1 : 1);
+                    S.psi[j][c - 1] = pm;
                     const float Tm = 2.0f * (y < 1 ? d.T_H : d.T_C) - S.T[js][c - 1];
                     S.T[j][c - 1] = Tm;
-                    S.sig[j][c - 1] = sigma_eos(d, Tm, S.psi[js][c - 1]);
+                    S.sig[j][c - 1] = sigma_eos(d, Tm, pm);
                 }
             }
             __syncthreads();
@@ -1422,7 +1435,8 @@ __global__ void init_dev_kernel(LbmDev d, const float* __restrict__ fld, S* __re
 }
 
 // Analytic initial fields: tanh bubble (Sec. 3 profile), fluid at rest, T
-// linear between the wall planes, uniform psi.
+// linear between the wall planes, psi uniform (psi0) or, with psi_bc 1 or 2,
+// linear from psi_L to psi_R between the wall planes.
 __global__ void analytic_fields_kernel(LbmDev d, float* __restrict__ fld)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1437,13 +1451,16 @@ __global__ void analytic_fields_kernel(LbmDev d, float* __restrict__ fld)
     }
     float T = d.T_ref;
     if (d.walls) T = d.T_H + (d.T_C - d.T_H) * ((float)y - 0.5f) / (float)(d.ny - 2);
+    float psi = d.psi0;
+    if (d.walls && d.psi_bc != 0)
+        psi = d.psi_L + (d.psi_R - d.psi_L) * ((float)y - 0.5f) / (float)(d.ny - 2);
     const bool fluid = !d.walls || (y >= 1 && y <= d.ny - 2);
     fld[o] = fluid ? phi : 0.0f;
     fld[N + o] = 0.0f;
     fld[2 * N + o] = 0.0f;
     fld[3 * N + o] = 0.0f;
     fld[4 * N + o] = fluid ? T : 0.0f;
-    fld[5 * N + o] = fluid ? d.psi0 : 0.0f;
+    fld[5 * N + o] = fluid ? psi : 0.0f;
 }
 
 __device__ __forceinline__ double warp_sum(double v)

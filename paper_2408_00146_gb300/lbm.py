@@ -34,7 +34,10 @@ PARAM_FIELDS = [
     ("Fext_x", ctypes.c_double), ("Fext_y", ctypes.c_double),
     ("gravity", ctypes.c_double), ("nu_A", ctypes.c_double),
     ("alpha_A", ctypes.c_double), ("precision", ctypes.c_int32),
+    ("psi_L", ctypes.c_double), ("psi_R", ctypes.c_double), ("psi_bc", ctypes.c_int32),
 ]
+# fields a parameter dict may leave out (0 if absent)
+OPTIONAL = ("precision", "psi_L", "psi_R", "psi_bc")
 
 OBS_FIELDS = ["t", "mass_phi", "mass_psi", "xc", "yc", "ux_bub", "uy_bub", "U_o", "t_star"]
 
@@ -129,7 +132,7 @@ def _check(status: int, where: str):
 def make_params(d: dict) -> LbmParams:
     p = LbmParams()
     for name, _ in PARAM_FIELDS:
-        setattr(p, name, d.get(name, 0) if name == "precision" else d[name])
+        setattr(p, name, d.get(name, 0) if name in OPTIONAL else d[name])
     return p
 
 
