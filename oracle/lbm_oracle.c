@@ -41,6 +41,11 @@
  *       T_w) for h; stencil ghosts at and beyond the walls are the mirror
  *       images about the wall plane (even for phi, psi, p*, odd about T_w
  *       for T).
+ *   R14 the properties rho, mu, alpha are interpolated (R2) with phi clamped
+ *       to [0, 1]: the conservative phase field overshoots 1 by ~1e-3 inside
+ *       a bubble, and at the paper's density ratio of 1000 an overshoot of
+ *       1e-3 already makes rho <= 0 (the step then diverges within tens of
+ *       steps).  phi itself, and every other use of it, stays unclamped.
  *   R13 surfactant held at psi_L (y = 0 end) and psi_R (y = ny-1 end), the
  *       paper's setting of its main cases (Sec. 2, Sec. 6): q takes the
  *       anti-bounce-back Dirichlet rule of h with psi_w, and psi's stencil
@@ -403,19 +408,25 @@ static double psi_at(const orc_sim* s, int x, int y)
     return v;
 }
 
+/* phi for the property interpolation (R14): clamped to [0, 1]. */
+static double phi_prop(double phi)
+{
+    return phi < 0.0 ? 0.0 : (phi > 1.0 ? 1.0 : phi);
+}
+
 static double rho_of(const orc_sim* s, double phi)
 {
-    return s->d.rho_A + phi * (s->d.rho_B - s->d.rho_A); /* Eq. (17), R2 */
+    return s->d.rho_A + phi_prop(phi) * (s->d.rho_B - s->d.rho_A); /* Eq. (17), R2, R14 */
 }
 
 static double mu_of(const orc_sim* s, double phi)
 {
-    return s->d.mu_A + phi * (s->d.mu_B - s->d.mu_A); /* Eq. (17), R2 */
+    return s->d.mu_A + phi_prop(phi) * (s->d.mu_B - s->d.mu_A); /* Eq. (17), R2, R14 */
 }
 
 static double alpha_of(const orc_sim* s, double phi)
 {
-    return s->d.alpha_A + phi * (s->d.alpha_B - s->d.alpha_A);
+    return s->d.alpha_A + phi_prop(phi) * (s->d.alpha_B - s->d.alpha_A);
 }
 
 static double sigma_at(const orc_sim* s, int x, int y)
