@@ -165,9 +165,10 @@ lbm_status lbm_create_ex(const lbm_params* p, void* stream, void* workspace,
  *     T, psi; every population is set to the equilibrium of App. B-E built
  *     from these fields (n and R from the isotropic stencils of phi);
  *   else: the analytic state of Sec. 2 -- bubble of radius R at (xb, yb) with
- *     the tanh profile of Sec. 3, fluid at rest, T linear from T_H on the
- *     plane y = 1/2 to T_C on y = ny - 3/2 (T_ref without walls), psi = psi0,
- *     then the equilibria as above.
+ *     the tanh profile of Sec. 3, fluid at rest (p = 0), T linear from T_H
+ *     on the plane y = 1/2 to T_C on y = ny - 3/2 (T_ref without walls),
+ *     psi = psi0 (or the psi_L -> psi_R profile, see psi_bc), then the
+ *     equilibria as above.
  * Errors: LBM_EINVAL (NULL sim), LBM_ECUDA. */
 lbm_status lbm_init(lbm_sim* sim, const double* fields, const float* populations);
 

@@ -71,6 +71,11 @@ __device__ __forceinline__ float psi_ghost(const LbmDev& d, float psi, int side)
     return 2.0f * (side < 0 ? d.psi_L : d.psi_R) - psi;
 }
 
+// The properties rho, mu, alpha are interpolated linearly in phi (Eq. (17))
+// with phi clamped to [0, 1] (__saturatef): the conservative phase field
+// overshoots 1 by ~1e-3 inside a bubble, which at a density ratio of 1000
+// would make rho_B + (phi - 1)(rho_B - rho_A) negative.
+
 // Surface tension law, Eq. (6); ln(1 - psi) with psi clamped to [0, 1-1e-6].
 __device__ __forceinline__ float sigma_eos(const LbmDev& d, float T, float psi)
 {
@@ -431,7 +436,7 @@ __device__ __forceinline__ NodeMoments own_moments(const LbmDev& d, const TileSm
     if (side > 0) Tg = 2.0f * d.T_C - m.T;
     sm.phi[ty + 2][tx + 2] = m.phi;
     sm.sig[ty + 1][tx + 1] = sigma_eos(d, Tg, psi_ghost(d, m.psi, side));
-    sm.phs[ty + 1][tx + 1] = m.pst - (d.rhoA + m.phi * d.drho) * kCs2;
+    sm.phs[ty + 1][tx + 1] = m.pst - (d.rhoA + __saturatef(m.phi) * d.drho) * kCs2;
     return m;
 }
 
@@ -446,7 +451,7 @@ __device__ __forceinline__ void halo_fields(const LbmDev& d, const TileSmem& sm,
         if (side < 0) Th = 2.0f * d.T_H - Th;
         if (side > 0) Th = 2.0f * d.T_C - Th;
         sm.sig[ey - 1][ex - 1] = sigma_eos(d, Th, psi_ghost(d, sp, side));
-        sm.phs[ey - 1][ex - 1] = ps - (d.rhoA + ph * d.drho) * kCs2;
+        sm.phs[ey - 1][ex - 1] = ps - (d.rhoA + __saturatef(ph) * d.drho) * kCs2;
     }
 }
 
@@ -505,7 +510,7 @@ __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
     const float ndots = n_x * sgx + n_y * sgy;
     const float deltas = d.deltas_coef * g2;
     const float phi = m.phi, T = m.T, psi = m.psi;
-    const float rho = d.rhoA + phi * d.drho;
+    const float rho = d.rhoA + __saturatef(phi) * d.drho;
     const float inv_rho = __fdividef(1.0f, rho);
     const float Ftx = deltas * (-sig * kappa * n_x + sgx - n_x * ndots) + d.Fext_x;
     const float Fty = deltas * (-sig * kappa * n_y + sgy - n_y * ndots) + d.Fext_y -
@@ -543,7 +548,7 @@ __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
     {
 #pragma unroll
         for (int a = 0; a < 9; ++a) v[a] = own(18 + a);
-        const float alpha = d.alphaA + phi * d.dalpha;
+        const float alpha = d.alphaA + __saturatef(phi) * d.dalpha;
         const float wT = __fdividef(1.0f, 3.0f * alpha + 0.5f);
         scalar_collide(v, T, 0.0f, 0.0f, wT, ux, uy);
         Mh = st.template put<true>(2, N, nb, v, T, wall, wall < 0 ? d.T_H : d.T_C);
@@ -564,7 +569,7 @@ __device__ __forceinline__ void node_update(const LbmDev& d, const TileSmem& sm,
     {
 #pragma unroll
         for (int a = 0; a < 9; ++a) v[a] = own(9 + a);
-        const float mu = d.muA + phi * d.dmu;
+        const float mu = d.muA + __saturatef(phi) * d.dmu;
         const float wn = __fdividef(1.0f, 3.0f * mu * inv_rho + 0.5f);
         const float vp = p - rho * kCs2;                      // varphi = p - rho c_s^2
         const float ux2 = ux * ux, uy2 = uy * uy;
@@ -767,7 +772,7 @@ __device__ __forceinline__ void equilibrium_set(const LbmDev& d, const float* __
     const float phi = fld[o], ux = fld[N + o], uy = fld[2 * N + o], p = fld[3 * N + o];
     const float T = fld[4 * N + o], psi = fld[5 * N + o];
     if (s == 1) {
-        const float rho = d.rhoA + phi * d.drho;
+        const float rho = d.rhoA + __saturatef(phi) * d.drho;
         const float vp = p - rho * kCs2;
         const float ux2 = ux * ux, uy2 = uy * uy;
         central_to_pop(p, -vp * ux, -vp * uy, p * kCs2 + vp * ux2, p * kCs2 + vp * uy2,
@@ -1183,7 +1188,7 @@ __device__ __forceinline__ void stream_strip(const LbmDev& d, float* __restrict_
             for (int a = 0; a < 36; ++a) pv[a] = S.pop[st][a][rb][tx];
             m = pop_moments(OwnRegs{pv});
             S.phi[4 + rb][tx + 2] = m.phi;
-            S.phs[4 + rb][tx + 1] = m.pst - (d.rhoA + m.phi * d.drho) * kCs2;
+            S.phs[4 + rb][tx + 1] = m.pst - (d.rhoA + __saturatef(m.phi) * d.drho) * kCs2;
             S.T[4 + rb][tx + 1] = m.T;
             S.psi[4 + rb][tx + 1] = m.psi;
             S.sig[4 + rb][tx + 1] = sigma_eos(d, m.T, m.psi);
@@ -1211,7 +1216,7 @@ __device__ __forceinline__ void stream_strip(const LbmDev& d, float* __restrict_
                     const float s2 = sum9(v);
                     if (f == 0) {
                         S.phi[4 + r][c + 1] = s1;
-                        S.phs[4 + r][c] = s2 - (d.rhoA + s1 * d.drho) * kCs2;
+                        S.phs[4 + r][c] = s2 - (d.rhoA + __saturatef(s1) * d.drho) * kCs2;
                     } else {
                         S.T[4 + r][c] = s1;
                         S.psi[4 + r][c] = s2;

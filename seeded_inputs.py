@@ -102,16 +102,13 @@ def bubble_fields(p: dict, seed: int | None = None, psi_noise: float = 0.0,
                   u_noise: float = 0.0, T_noise: float = 0.0,
                   p_noise: float = 0.0) -> np.ndarray:
     """Circular bubble (phi = 1 inside) of radius R at (xb, yb) with the
-    hyperbolic-tangent interface profile, u = 0, the Laplace pressure jump of
-    a resting bubble p = phi sigma0 / R (sigma0 the clean-interface value),
-    linear wall-to-wall T and the initial psi of initial_psi, plus optional
-    seeded uniform noise on psi, u, T and p."""
+    hyperbolic-tangent interface profile, u = 0, p = 0, linear wall-to-wall T
+    and the initial psi of initial_psi, plus optional seeded uniform noise on
+    psi, u, T and p."""
     x, y = _grid(p)
     r = np.hypot(x - p["xb"], y - p["yb"])
     out = np.zeros((6, p["ny"], p["nx"]))
     out[0] = 0.5 + 0.5 * np.tanh(2.0 * (p["R"] - r) / p["W"]) if p["R"] > 0 else 0.0
-    if p["R"] > 0:
-        out[3] = out[0] * p["sigma0"] / p["R"]
     out[4] = linear_wall_temperature(p)
     out[5] = initial_psi(p)
     if seed is not None:

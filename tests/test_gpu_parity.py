@@ -270,3 +270,21 @@ def test_batched_step_equals_separate_steps(lbm):
         assert np.array_equal(a.populations(), b.populations())
     with pytest.raises(lbm.LbmError):
         lbm.lbm_step_batch([batch[0], batch[0]], 1)
+
+
+@pytest.mark.parametrize("nx", [64, 40])
+def test_buoyancy_term_matches_oracle(lbm, orc, nx):
+    """The buoyancy force -(rho - rho_A) g of Sec. 5.3 (density ratio 10):
+    streaming kernel (nx = 64) and tile kernel (nx = 40) against the
+    oracle after 1 and 40 steps."""
+    p = si.scaled_channel(nx, 64)
+    p.update(R=7.0, gravity=2e-5)
+    f = si.parity_fields(p, seed=11)
+    sim, o = _pair(lbm, orc, p, f)
+    for n in (1, 40):
+        sim.step(n)
+        o.step(n)
+        ferr = _field_errors(sim.fields(), o.fields(), p)
+        assert max(ferr.values()) < 1e-4, (n, ferr)
+    a, b = sim.observe(), o.observe()
+    assert a["uy_bub"] == pytest.approx(b["uy_bub"], rel=1e-3, abs=1e-7)
