@@ -292,9 +292,10 @@ void plan_for_length(const int* nch, int n, int L, int* plan)
 }
 
 // The model: a strip of L chunks costs about L + 2 chunk-times (the chunk
-// below it is read first, plus start-up); strips run on 2 x num_sms block
-// slots in launch order, longest first, a slot taking the next strip when it
-// frees.  Returns the predicted launch time in chunk-times.
+// below it is read first, plus start-up); strips run on the streaming
+// kernel's resident block slots (stream_blocks_per_sm() x num_sms) in launch
+// order, longest first, a slot taking the next strip when it frees.  Returns
+// the predicted launch time in chunk-times.
 double predicted_span(const int* nch, const int* ncol, int n, const int* plan, int slots)
 {
     std::vector<int> lens;
@@ -389,7 +390,7 @@ void plan_strips(const LbmDev* const* devs, int n, int num_sms, int* out)
         return;
     }
     const int maxch = std::max(1, *std::max_element(nch, nch + n));
-    const int slots = 2 * std::max(num_sms, 1);
+    const int slots = stream_blocks_per_sm() * std::max(num_sms, 1);
     long long cols = 0;
     for (int i = 0; i < n; ++i) cols += ncol[i];
     const bool multi_wave = cols > slots;

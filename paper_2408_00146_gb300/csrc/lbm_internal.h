@@ -112,6 +112,8 @@ struct StreamBatchArgs {
 cudaError_t prepare_stream();
 bool stream_eligible(const LbmDev& d);
 int stream_columns(const LbmDev& d);
+// Resident blocks per SM of the streaming kernel (its launch bounds).
+int stream_blocks_per_sm();
 int stream_blocks(const LbmDev& d, int strip_chunks);
 cudaError_t launch_stream_batch(const StreamBatchArgs& args, cudaStream_t s);
 

@@ -1734,6 +1734,8 @@ bool stream_eligible(const LbmDev& d)
 
 int stream_columns(const LbmDev& d) { return d.nx / kTileX; }
 
+int stream_blocks_per_sm() { return 2; }
+
 int stream_blocks(const LbmDev& d, int strip_chunks)
 {
     const int ncol = d.nx / kTileX;
