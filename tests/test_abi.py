@@ -55,6 +55,7 @@ def test_derived_parameters_match_oracle(orc, cfg):
 @pytest.mark.parametrize("bad", [
     dict(nx=3), dict(ny=4), dict(M_phi=-0.1), dict(R=40.0), dict(W=0.0),
     dict(precision=7), dict(sigma_TT=0.0), dict(walls=2), dict(nx=100000, ny=100000),
+    dict(psi_bc=3), dict(psi_bc=-1), dict(psi_bc=1, psi_L=1.0), dict(psi_bc=2, psi_R=-0.5),
 ])
 def test_invalid_parameters_rejected(bad):
     from paper_2408_00146_gb300 import lbm
@@ -83,3 +84,13 @@ def test_workspace_bytes_layout():
         assert ws16 >= (2 * (36 * 2 + 16) + 6 * 4) * n
         assert ws16 < (2 * (36 * 2 + 16) + 6 * 4) * n + 64 * 1024
         assert lbm.lbm_derive(q)["U_o"] == lbm.lbm_derive(p)["U_o"]
+
+
+def test_batch_calls_reject_empty_batches_on_the_host():
+    """Argument checks of the batch entry points run before any CUDA call."""
+    from paper_2408_00146_gb300 import lbm
+    for call in (lambda: lbm.lbm_step_batch([], 1), lambda: lbm.lbm_tune_batch([], 1),
+                 lambda: lbm.lbm_batch_plan([])):
+        with pytest.raises(lbm.LbmError) as ei:
+            call()
+        assert ei.value.status == lbm.LBM_EINVAL
