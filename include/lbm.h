@@ -211,9 +211,10 @@ lbm_status lbm_batch_plan(lbm_sim* const* sims, int32_t n, int32_t* strip_chunks
  * host thread (a plan cache of 16 size lists; tuned plans are evicted last).
  * The trial steps are real steps: a step's result does not depend on the
  * plan, so every sim advances *steps_taken steps (1 untimed warm-up step +
- * trial_steps per candidate), as if by lbm_step_batch.  A batch with no
- * streaming sim takes no step.  Synchronises the stream.  The paper has no
- * counterpart.  Errors: LBM_EINVAL (trial_steps < 1, steps_taken NULL, batch
+ * trial_steps per candidate), as if by lbm_step_batch; on failure it still
+ * counts the steps taken.  A batch with no streaming sim takes no step.  Uses
+ * the caller's current device, as every call does.  Synchronises the stream.
+ * The paper has no counterpart.  Errors: LBM_EINVAL (trial_steps < 1, steps_taken NULL, batch
  * arguments), LBM_ESTATE, LBM_ECUDA. */
 lbm_status lbm_tune_batch(lbm_sim* const* sims, int32_t n, int32_t trial_steps,
                           int64_t* steps_taken);

@@ -885,13 +885,13 @@ lbm_status lbm_tune_batch(lbm_sim* const* sims, int32_t n, int32_t trial_steps, 
         plan_for_length(nch, sn, L, plan.data());
         if (std::find(plans.begin(), plans.end(), plan) == plans.end()) plans.push_back(plan);
     }
-    cudaSetDevice(sims[0]->device);
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaError_t e = cudaEventCreate(&ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
-    // one untimed step first, so that the first candidate is not timed cold
+    // one untimed step first, so that the first candidate is not timed cold;
+    // every batch step advances all sims together, so sims[0]->t counts them
+    const int64_t t0 = sims[0]->t;
     if (e == cudaSuccess) st = step_batch(sims, n, 1, model);
-    int64_t steps = 1;
     float best_ms = 0.0f;
     size_t best = 0;
     for (size_t c = 0; c < plans.size() && e == cudaSuccess && st == LBM_OK; ++c) {
@@ -899,7 +899,6 @@ lbm_status lbm_tune_batch(lbm_sim* const* sims, int32_t n, int32_t trial_steps, 
         if (e != cudaSuccess) break;
         st = step_batch(sims, n, trial_steps, plans[c].data());
         if (st != LBM_OK) break;
-        steps += trial_steps;
         e = cudaEventRecord(ev[1], sims[0]->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
         float ms = 0.0f;
@@ -911,7 +910,7 @@ lbm_status lbm_tune_batch(lbm_sim* const* sims, int32_t n, int32_t trial_steps, 
     }
     for (cudaEvent_t x : ev)
         if (x) cudaEventDestroy(x);
-    *steps_taken = steps;
+    *steps_taken = sims[0]->t - t0;
     if (st != LBM_OK) return st;
     if (e != cudaSuccess) return fail(LBM_ECUDA, "lbm_tune_batch: %s", cudaGetErrorString(e));
     store_plan(nch, ncol, sn, sg[0]->num_sms, plans[best].data(), true);
