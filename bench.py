@@ -292,7 +292,9 @@ def run_gpu(args) -> None:
         barrier()
         l0 = sum(s.launches() for s in sims)
         ev0.record(stream)
-        if args.graph and args.mode == "plain":
+        if args.mode == "batched" and not args.per_step_calls:
+            lbm.lbm_step_batch(sims, nsteps)  # one call: replayed CUDA graphs of 64 steps
+        elif args.graph and args.mode == "plain":
             for s in sims:                   # all steps in one call: CUDA-graph replay
                 s.step(nsteps)
         else:
@@ -307,8 +309,15 @@ def run_gpu(args) -> None:
     if args.mode == "batched" and args.tune_steps > 0:
         tuned_steps = lbm.lbm_tune_batch(sims, args.tune_steps)
     plan = lbm.lbm_batch_plan(sims)
-    for _ in range(args.warmup):
-        step_all()
+    warmup_run = args.warmup
+    if args.mode == "batched" and not args.per_step_calls:
+        # at least one 64-step run, so that the batch's graph is captured
+        # before the timed region
+        warmup_run = max(args.warmup, 64)
+        lbm.lbm_step_batch(sims, warmup_run)
+    else:
+        for _ in range(args.warmup):
+            step_all()
     with ClockSampler(dev_index) as clk:
         ms, launches = timed(args.steps)
     clocks = clk.summary()
@@ -353,7 +362,10 @@ def run_gpu(args) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "lattices": [f"{p['nx']}x{p['ny']}" for p in params],
                        "sims_per_gpu": len(params), "fluid_nodes_per_step": nodes_per_step,
-                       "launch_mode": args.mode + (" graph" if args.graph and args.mode == "plain" else ""),
+                       "launch_mode": args.mode + (" graph" if (args.graph and args.mode == "plain") or
+                                                   (args.mode == "batched" and not args.per_step_calls)
+                                                   else ""),
+                       "warmup_steps_run": warmup_run,
                        "other_mode": other,
                        "strip_plan": {"tuned": tuned_steps > 0, "tuning_steps": tuned_steps,
                                       "strip_chunks": sorted(set(plan) - {0})},
@@ -420,10 +432,10 @@ def run_e2e(args, lbm, torch, stream, params) -> dict:
     done = 0
     while done < steps:
         n = min(100, steps - done)
-        for _ in range(n):             # interleaved, as in the device-timed loop
-            if args.mode == "batched":
-                lbm.lbm_step_batch(sims, 1)
-            else:
+        if args.mode == "batched":
+            lbm.lbm_step_batch(sims, n)   # as in the device-timed loop
+        else:
+            for _ in range(n):            # interleaved, as in the device-timed loop
                 for s in sims:
                     s.step(1)
         for s in sims:
@@ -460,6 +472,9 @@ def main():
     ap.add_argument("--graph", action="store_true",
                     help="plain mode: advance each simulation by all timed steps in one "
                          "lbm_step call (replayed CUDA graphs of 64 steps)")
+    ap.add_argument("--per-step-calls", action="store_true",
+                    help="batched mode: one lbm_step_batch call per step instead of one call for "
+                         "all timed steps (no CUDA-graph replay)")
     ap.add_argument("--compare-modes", action="store_true", default=True)
     ap.add_argument("--tune-steps", type=int, default=10,
                     help="batched mode: steps per candidate strip plan for lbm_tune_batch "

@@ -15,6 +15,7 @@
 #include <functional>
 #include <vector>
 #include <algorithm>
+#include <atomic>
 #include <utility>
 
 namespace {
@@ -222,6 +223,7 @@ struct lbm_sim {
     CUtensorMap tside[2];
     int strip_chunks;  // chunks per strip when stepped alone
     int num_sms;
+    uint64_t id;       // unique over the process, never reused
 };
 
 namespace {
@@ -426,6 +428,8 @@ static lbm_status create_impl(const lbm_params* p, void* stream, void* ws, size_
         return fail(LBM_EINVAL, "workspace must be 256-byte aligned");
     lbm_sim* s = new (std::nothrow) lbm_sim();
     if (!s) return fail(LBM_ENOMEM, "host allocation failed");
+    static std::atomic<uint64_t> next_id{1};
+    s->id = next_id.fetch_add(1);
     s->p = *p;
     std::memcpy(s->derived, dv, sizeof dv);
     s->dev = make_dev(p, dv);
@@ -771,8 +775,36 @@ static int stream_group(lbm_sim* const* sims, int n, lbm_sim** stream, int* plan
     return sn;
 }
 
+// Captured CUDA graphs of kGraphSteps batched steps, per host thread, keyed
+// by the sims (their unique ids, which are never reused, in argument order),
+// the buffer each sim starts from, and the strip plan.  A graph whose sims
+// have been destroyed can never match again; it is destroyed when evicted
+// (cudaGraphExecDestroy lets a replay still in flight finish).
+struct BatchGraph {
+    int n = 0, sn = 0;
+    uint64_t id[kMaxBatch];
+    int cur[kMaxBatch], plan[kMaxBatch];
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+constexpr int kBatchGraphs = 8;
+static thread_local BatchGraph batch_graphs[kBatchGraphs];
+static thread_local int batch_graph_next = 0;
+
+static BatchGraph* find_batch_graph(lbm_sim* const* sims, int n, const int* plan, int sn)
+{
+    for (BatchGraph& g : batch_graphs) {
+        if (!g.exec || g.n != n || g.sn != sn || g.stream != sims[0]->stream) continue;
+        bool same = std::memcmp(g.plan, plan, sizeof(int) * sn) == 0;
+        for (int i = 0; i < n && same; ++i) same = g.id[i] == sims[i]->id && g.cur[i] == sims[i]->cur;
+        if (same) return &g;
+    }
+    return nullptr;
+}
+
 // nsteps batched steps; forced (optional) replaces the planned strip lengths
-// of the streaming group (one per streaming sim, in argument order).
+// of the streaming group (one per streaming sim, in argument order).  Runs of
+// kGraphSteps steps with the planned strips replay a captured graph.
 static lbm_status step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps, const int* forced)
 {
     // one launch per kernel family present: the streaming kernel for the
@@ -789,10 +821,15 @@ static lbm_status step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps, co
     int schunks[kMaxBatch];
     const int sn = stream_group(sims, n, sgroup, schunks);
     if (forced) std::memcpy(schunks, forced, sizeof(int) * sn);
+    const int plan_key_chunks = sn;
+    int plan_in_arg_order[kMaxBatch];
+    std::memcpy(plan_in_arg_order, schunks, sizeof(int) * sn);
+    int kernels = sn > 0 ? 1 : 0;   // launches per step
     for (int i = 0; i < n; ++i) {
         if (sims[i]->ystream) continue;
         const int k = sims[i]->p.precision;
         BatchArgs& a = args[k];
+        if (a.n == 0) ++kernels;
         group[k][a.n] = sims[i];
         a.dev[a.n] = sims[i]->dev;
         a.err[a.n] = sims[i]->err;
@@ -807,13 +844,14 @@ static lbm_status step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps, co
             std::swap(schunks[j], schunks[j - 1]);
             std::swap(sgroup[j], sgroup[j - 1]);
         }
-    for (int64_t step = 0; step < nsteps; ++step) {
+    // the kernels of one step from each sim's current buffer; flips the buffers
+    auto one_step = [&](cudaStream_t st) -> cudaError_t {
         if (sn > 0) {
             sargs.n = sn;
             sargs.first[0] = 0;
             for (int i = 0; i < sn; ++i) stream_entry(sargs, i, sgroup[i], sgroup[i]->cur, schunks[i]);
-            CUDA_TRY(launch_stream_batch(sargs, sims[0]->stream));
-            sims[0]->launches += 1;
+            cudaError_t e = launch_stream_batch(sargs, st);
+            if (e != cudaSuccess) return e;
         }
         for (int k = 0; k < 3; ++k) {
             BatchArgs& a = args[k];
@@ -827,16 +865,55 @@ static lbm_status step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps, co
                 a.has_tmap[i] = s->have_tmap ? 1 : 0;
                 if (s->have_tmap) a.tmap[i] = s->tmap[s->cur];
             }
-            if (k == LBM_FP32)
-                CUDA_TRY(launch_step_batch(a, tiles[k], sims[0]->stream));
-            else
-                CUDA_TRY(launch_step_batch_dev(a, k, tiles[k], sims[0]->stream));
-            sims[0]->launches += 1;
+            cudaError_t e = k == LBM_FP32 ? launch_step_batch(a, tiles[k], st)
+                                          : launch_step_batch_dev(a, k, tiles[k], st);
+            if (e != cudaSuccess) return e;
         }
-        for (int i = 0; i < n; ++i) {
-            sims[i]->cur ^= 1;
-            sims[i]->t += 1;
+        for (int i = 0; i < n; ++i) sims[i]->cur ^= 1;
+        return cudaSuccess;
+    };
+    int64_t left = nsteps;
+    if (!forced && left >= kGraphSteps) {
+        BatchGraph* g = find_batch_graph(sims, n, plan_in_arg_order, plan_key_chunks);
+        if (!g) {
+            int cur0[kMaxBatch];
+            for (int i = 0; i < n; ++i) cur0[i] = sims[i]->cur;
+            cudaStream_t cap = sims[0]->cap_stream;
+            CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) e = one_step(cap);
+            for (int i = 0; i < n; ++i) sims[i]->cur = cur0[i];   // capture ran nothing
+            cudaGraph_t graph = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+            cudaGraphExec_t exec = nullptr;
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail(LBM_ECUDA, "batch capture: %s", cudaGetErrorString(e));
+            g = &batch_graphs[batch_graph_next];
+            batch_graph_next = (batch_graph_next + 1) % kBatchGraphs;
+            if (g->exec) cudaGraphExecDestroy(g->exec);
+            g->n = n;
+            g->sn = plan_key_chunks;
+            for (int i = 0; i < n; ++i) {
+                g->id[i] = sims[i]->id;
+                g->cur[i] = cur0[i];
+            }
+            std::memcpy(g->plan, plan_in_arg_order, sizeof(int) * plan_key_chunks);
+            g->stream = sims[0]->stream;
+            g->exec = exec;
         }
+        while (left >= kGraphSteps) {   // an even number of steps: buffers return
+            CUDA_TRY(cudaGraphLaunch(g->exec, sims[0]->stream));
+            left -= kGraphSteps;
+            sims[0]->launches += (int64_t)kGraphSteps * kernels;
+            for (int i = 0; i < n; ++i) sims[i]->t += kGraphSteps;
+        }
+    }
+    for (; left > 0; --left) {
+        CUDA_TRY(one_step(sims[0]->stream));
+        sims[0]->launches += kernels;
+        for (int i = 0; i < n; ++i) sims[i]->t += 1;
     }
     return LBM_OK;
 }

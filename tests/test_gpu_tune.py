@@ -80,3 +80,29 @@ def test_tune_without_streaming_sims_and_bad_arguments(lbm):
     with pytest.raises(lbm.LbmError):
         lbm.lbm_tune_batch([sims[0], sims[0]], 1)
     assert sims[0].observe()["t"] == 0
+
+
+def test_graph_replayed_batch_equals_single_steps(lbm):
+    """lbm_step_batch replays a captured graph for runs of 64 steps; its
+    result and launch count equal those of the same steps issued one call
+    at a time, with the sims starting from different buffers and a graph
+    taken again from the cache."""
+    import torch
+    ps = _mix()
+    st = torch.cuda.Stream()
+    a, b = _sims(lbm, ps, st), _sims(lbm, ps, st)
+    a[1].step(1)
+    b[1].step(1)
+    l0a, l0b = a[0].launches(), b[0].launches()
+    lbm.lbm_step_batch(a, 130)
+    for _ in range(130):
+        lbm.lbm_step_batch(b, 1)
+    assert a[0].launches() - l0a == b[0].launches() - l0b
+    for x, y in zip(a, b):
+        assert np.array_equal(x.populations(), y.populations())
+    lbm.lbm_step_batch(a, 64)
+    lbm.lbm_step_batch(b[:2], 64)       # another batch in between
+    lbm.lbm_step_batch(b[2:], 64)
+    for x, y in zip(a, b):
+        assert np.array_equal(x.populations(), y.populations())
+        assert x.observe()["t"] == y.observe()["t"]
