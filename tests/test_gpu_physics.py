@@ -106,3 +106,26 @@ def test_mass_conserved_over_20000_steps(lbm, precision, rel):
     assert b["mass_phi"] == pytest.approx(a["mass_phi"], rel=rel)
     assert b["mass_psi"] == pytest.approx(a["mass_psi"], rel=rel)
     assert b["nan_flag"] == 0
+
+
+def test_gibbs_term_opposes_thermocapillary_migration(lbm):
+    """Sec. 6 trend on the 256 x 1024 channel of the sweep (density ratio
+    10, SRF law sigma_TT = 2e-3, surfactant held at psi_L = 0.4 and
+    psi_R = 0.1): after 50000 steps the clean bubble (beta = 0) has moved
+    towards the reference-temperature plane at mid-channel, and a Gibbs
+    term pulls it back upstream the more, the larger beta (the surfactant
+    Marangoni stress against the thermocapillary one)."""
+    import torch
+    st = torch.cuda.Stream()
+    sims = []
+    for beta in (0.0, 0.2, 0.4):
+        p = si.channel_256x1024(beta, 2e-3)
+        p.update(psi_bc=1, psi_L=0.4, psi_R=0.1)
+        s = lbm.Sim(p, stream=st)
+        s.init()
+        sims.append(s)
+    y0 = sims[0].observe()["yc"]
+    lbm.lbm_step_batch(sims, 50000)
+    y = [s.observe()["yc"] for s in sims]
+    assert y[0] > y0 + 2.0, (y0, y)
+    assert y[0] > y[1] + 2.0 and y[1] > y[2] + 1.0, y
