@@ -129,3 +129,28 @@ def test_gibbs_term_opposes_thermocapillary_migration(lbm):
     y = [s.observe()["yc"] for s in sims]
     assert y[0] > y0 + 2.0, (y0, y)
     assert y[0] > y[1] + 2.0 and y[1] > y[2] + 1.0, y
+
+
+def test_sec6_srf_ordering_with_the_papers_parameters(lbm):
+    """The SRF parameters of Sec. 6 (M2 = 5, Re = 5, Ma = 0.25, W = 5,
+    surfactant held at psi_L / psi_R = 0.1) at density ratio 10 on the
+    256 x 1024 channel, to t* = 40: the clean bubble runs ahead towards the
+    reference-temperature plane, beta = 0.4 holds it back, and a steeper
+    surfactant gradient (psi_L = 0.6 instead of 0.4) holds it back further
+    -- the ordering of the paper's equilibrium positions (0.5, ~0.45, ~0.4),
+    which the full run to t* = 1000 reproduces (0.500, 0.442, 0.394)."""
+    import torch
+    st = torch.cuda.Stream()
+    sims = []
+    for beta, psiL in ((0.0, 0.4), (0.4, 0.4), (0.4, 0.6)):
+        p = si.channel_256x1024(beta, 0.025)
+        p.update(Re=5.0, Ma=0.25, W=5.0, psi_bc=1, psi_L=psiL, psi_R=0.1)
+        s = lbm.Sim(p, stream=st)
+        s.init()
+        sims.append(s)
+    d = sims[0].derived()
+    y0 = sims[0].observe()["yc"]
+    lbm.lbm_step_batch(sims, int(40.0 * 32.0 / d["U_o"]))
+    y = [s.observe()["yc"] for s in sims]
+    assert all(v > y0 + 10.0 for v in y), (y0, y)
+    assert y[0] > y[1] + 10.0 and y[1] > y[2] + 5.0, y
