@@ -154,3 +154,25 @@ def test_sec6_srf_ordering_with_the_papers_parameters(lbm):
     y = [s.observe()["yc"] for s in sims]
     assert all(v > y0 + 10.0 for v in y), (y0, y)
     assert y[0] > y[1] + 10.0 and y[1] > y[2] + 5.0, y
+
+
+def test_sec6_normal_fluid_terminal_velocity_falls_with_beta(lbm):
+    """The normal-fluid case of Sec. 6 (M1 = -2.5, M2 = 0, psi_L = 0.1,
+    psi_R = 0.4, start at 0.75 L) at density ratio 10: the bubble runs
+    towards the hot wall (U < 0) and the Gibbs term slows it (measured to
+    t* = 180: U/U_o = -0.106 at beta = 0, -0.083 at beta = 0.4)."""
+    import torch
+    st = torch.cuda.Stream()
+    sims = []
+    for beta in (0.0, 0.4):
+        p = si.channel_256x1024(beta, 0.0)
+        p.update(sigma_T=-2.5 * 5e-3, Re=5.0, Ma=0.25, W=5.0, psi_bc=1, psi_L=0.1, psi_R=0.4,
+                 yb=0.5 + 0.75 * 1022)
+        s = lbm.Sim(p, stream=st)
+        s.init()
+        sims.append(s)
+    Uo = sims[0].derived()["U_o"]
+    lbm.lbm_step_batch(sims, int(40.0 * 32.0 / Uo))
+    u = [s.observe()["uy_bub"] / Uo for s in sims]
+    assert u[0] < u[1] < 0.0, u
+    assert abs(u[0]) - abs(u[1]) > 0.05 * abs(u[0]), u
