@@ -75,48 +75,84 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+def _bind(L):
+    """Argument and result types of every exported oracle function."""
+    P, I64, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.orc_derive.argtypes = [ctypes.POINTER(OrcParams), ctypes.POINTER(OrcDerived)]
+    L.orc_create.argtypes = [ctypes.POINTER(OrcParams), ctypes.POINTER(P)]
+    L.orc_destroy.argtypes = [P]
+    L.orc_destroy.restype = None
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    L.orc_init_fields.argtypes = [P, dp]
+    L.orc_set_populations.argtypes = [P, dp]
+    L.orc_get_populations.argtypes = [P, dp]
+    L.orc_step.argtypes = [P, I64]
+    L.orc_time.argtypes = [P]
+    L.orc_time.restype = I64
+    L.orc_fields.argtypes = [P, dp]
+    L.orc_observe.argtypes = [P, dp]
+    L.orc_matrix_P.argtypes = [dp]
+    L.orc_matrix_P.restype = None
+    L.orc_matrix_Pinv.argtypes = [dp]
+    L.orc_matrix_Pinv.restype = None
+    L.orc_matrix_F.argtypes = [D, D, dp]
+    L.orc_matrix_F.restype = None
+    L.orc_weights.argtypes = [dp]
+    L.orc_weights.restype = None
+    L.orc_velocities.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.orc_velocities.restype = None
+    L.orc_sigma_eos.argtypes = [ctypes.POINTER(OrcParams), D, D]
+    L.orc_sigma_eos.restype = D
+    L.orc_G.argtypes = [ctypes.POINTER(OrcDerived), D, D]
+    L.orc_G.restype = D
+    L.orc_dG.argtypes = [ctypes.POINTER(OrcDerived), D, D]
+    L.orc_dG.restype = D
+    L.orc_cm_collide.argtypes = [dp, D, D, dp, dp, dp, ctypes.c_int, D, D, dp]
+    L.orc_cm_collide.restype = None
+    L.orc_gradient_periodic.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(LIB)
-            P, I64, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
-            dp = ctypes.POINTER(ctypes.c_double)
-            L.orc_derive.argtypes = [ctypes.POINTER(OrcParams), ctypes.POINTER(OrcDerived)]
-            L.orc_create.argtypes = [ctypes.POINTER(OrcParams), ctypes.POINTER(P)]
-            L.orc_destroy.argtypes = [P]
-            L.orc_destroy.restype = None
-            L.orc_set_threads.argtypes = [ctypes.c_int]
-            L.orc_init_fields.argtypes = [P, dp]
-            L.orc_set_populations.argtypes = [P, dp]
-            L.orc_get_populations.argtypes = [P, dp]
-            L.orc_step.argtypes = [P, I64]
-            L.orc_time.argtypes = [P]
-            L.orc_time.restype = I64
-            L.orc_fields.argtypes = [P, dp]
-            L.orc_observe.argtypes = [P, dp]
-            L.orc_matrix_P.argtypes = [dp]
-            L.orc_matrix_P.restype = None
-            L.orc_matrix_Pinv.argtypes = [dp]
-            L.orc_matrix_Pinv.restype = None
-            L.orc_matrix_F.argtypes = [D, D, dp]
-            L.orc_matrix_F.restype = None
-            L.orc_weights.argtypes = [dp]
-            L.orc_weights.restype = None
-            L.orc_velocities.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
-            L.orc_velocities.restype = None
-            L.orc_sigma_eos.argtypes = [ctypes.POINTER(OrcParams), D, D]
-            L.orc_sigma_eos.restype = D
-            L.orc_G.argtypes = [ctypes.POINTER(OrcDerived), D, D]
-            L.orc_G.restype = D
-            L.orc_dG.argtypes = [ctypes.POINTER(OrcDerived), D, D]
-            L.orc_dG.restype = D
-            L.orc_cm_collide.argtypes = [dp, D, D, dp, dp, dp, ctypes.c_int, D, D, dp]
-            L.orc_cm_collide.restype = None
-            L.orc_gradient_periodic.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
-            _lib = L
+            _lib = _bind(ctypes.CDLL(LIB))
     return _lib
+
+
+_variants: dict = {}
+
+
+def variant(tag: str, edits: list[tuple[str, str]]):
+    """The oracle with a planted mistake, for tests that show a pin fails on
+    it: a copy of lbm_oracle.c with each (old, new) text replaced (old must
+    occur exactly once), compiled like the oracle into its own library under
+    _build/variants/ and loaded beside it.  The oracle's source is untouched."""
+    with _lock:
+        if tag in _variants:
+            return _variants[tag]
+        with open(SRC) as fh:
+            src = fh.read()
+        for old, new in edits:
+            if src.count(old) != 1:
+                raise ValueError(f"variant {tag}: {old!r} occurs {src.count(old)} times")
+            src = src.replace(old, new)
+        vdir = os.path.join(HERE, "_build", "variants")
+        os.makedirs(vdir, exist_ok=True)
+        csrc = os.path.join(vdir, f"lbm_oracle_{tag}.c")
+        so = os.path.join(vdir, f"liboracle_{tag}.so")
+        with open(csrc, "w") as fh:
+            fh.write(src)
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-std=c11", "-Wall", "-I", HERE, "-o", so, csrc,
+                               "-lm"])
+        L = _bind(ctypes.CDLL(so))
+        L.orc_set_threads(os.cpu_count() or 1)
+        _variants[tag] = L
+        return L
 
 
 def _dp(a: np.ndarray):
@@ -222,11 +258,12 @@ def gradient_periodic(a: np.ndarray):
 class Oracle:
     """One FP64 simulation held by the oracle library."""
 
-    def __init__(self, params: dict):
+    def __init__(self, params: dict, library=None):
         self.params = dict(params)
+        self._L = library if library is not None else lib()
         self._p = make_params(params)
         h = ctypes.c_void_p()
-        rc = lib().orc_create(ctypes.byref(self._p), ctypes.byref(h))
+        rc = self._L.orc_create(ctypes.byref(self._p), ctypes.byref(h))
         if rc != 0:
             raise ValueError(f"orc_create rejected the parameters (code {rc})")
         self._h = h
@@ -234,7 +271,7 @@ class Oracle:
 
     def close(self):
         if self._h:
-            lib().orc_destroy(self._h)
+            self._L.orc_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -246,34 +283,34 @@ class Oracle:
     def init_fields(self, fields: np.ndarray):
         f = np.ascontiguousarray(fields, dtype=np.float64)
         assert f.shape == (6, self.ny, self.nx)
-        lib().orc_init_fields(self._h, _dp(f))
+        self._L.orc_init_fields(self._h, _dp(f))
 
     def set_populations(self, pops: np.ndarray):
         f = np.ascontiguousarray(pops, dtype=np.float64)
         assert f.shape == (4, 9, self.ny, self.nx)
-        lib().orc_set_populations(self._h, _dp(f))
+        self._L.orc_set_populations(self._h, _dp(f))
 
     def populations(self) -> np.ndarray:
         out = np.zeros((4, 9, self.ny, self.nx))
-        lib().orc_get_populations(self._h, _dp(out))
+        self._L.orc_get_populations(self._h, _dp(out))
         return out
 
     def step(self, n: int = 1):
-        rc = lib().orc_step(self._h, int(n))
+        rc = self._L.orc_step(self._h, int(n))
         if rc != 0:
             raise RuntimeError(f"orc_step failed ({rc})")
 
     @property
     def t(self) -> int:
-        return int(lib().orc_time(self._h))
+        return int(self._L.orc_time(self._h))
 
     def fields(self) -> np.ndarray:
         out = np.zeros((6, self.ny, self.nx))
-        lib().orc_fields(self._h, _dp(out))
+        self._L.orc_fields(self._h, _dp(out))
         return out
 
     def observe(self) -> dict:
         out = np.zeros(9)
-        lib().orc_observe(self._h, _dp(out))
+        self._L.orc_observe(self._h, _dp(out))
         keys = ["t", "mass_phi", "mass_psi", "xc", "yc", "ux_bub", "uy_bub", "U_o", "t_star"]
         return dict(zip(keys, out.tolist()))
