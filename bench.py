@@ -40,7 +40,7 @@ BYTES_PER_NODE_STEP = {"fp32": 288, "fp16": 176, "bf16": 176}
 BYTES_PER_NODE_BUFFER = {"fp32": 144, "fp16": 88, "bf16": 88}
 PRECISION_CODE = {"fp32": 0, "fp16": 1, "bf16": 2}
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-KERNEL_SRC = os.path.join(ROOT, "paper_2408_00146_gb300", "csrc", "lbm_kernels.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_2408_00146_gb300", "csrc", "lbm_stream.cu")
 
 
 def workload(name: str) -> list[dict]:
@@ -79,16 +79,20 @@ def kernel_hash() -> str:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def streams(p: dict) -> bool:
-    """Whether the library steps this FP32 lattice with the y-streaming
-    kernel (walls, nx a multiple of 32, at least 16 fluid rows)."""
-    return bool(p["walls"]) and p["nx"] % 32 == 0 and p["ny"] - 2 >= 16
+def streams(p: dict, precision: str) -> bool:
+    """Whether the library steps this lattice with a y-streaming kernel:
+    nx >= 32 and a multiple of 4 (FP32) or 8 (16-bit storage), at least 16 fluid rows,
+    walls or (FP32) a periodic y axis of whole 8-row chunks."""
+    nfy = p["ny"] - 2 if p["walls"] else p["ny"]
+    if p["nx"] % (4 if precision == "fp32" else 8) or p["nx"] < 32 or nfy < 16:
+        return False
+    return bool(p["walls"]) or (precision == "fp32" and nfy % 8 == 0)
 
 
 def step_kernel_name(mode: str, precision: str, params=None) -> str:
+    if params and all(streams(p, precision) for p in params):
+        return "stream32_kernel" if precision == "fp32" else "stream16_kernel"
     if precision == "fp32":
-        if params and all(streams(p) for p in params):
-            return "stream_batch_kernel"
         return "step_batch_kernel" if mode == "batched" else "step_kernel"
     return "step_batch_dev_kernel" if mode == "batched" else "step_dev_kernel"
 
@@ -210,48 +214,148 @@ def cpu_baseline(work: str, budget_s: float = 15.0) -> dict:
             "single_core_value": rate_1}
 
 
+def workload_config(work: str, params: list[dict], precision: str) -> dict:
+    """The workload as both arms name it (the GPU arm adds how it ran under
+    "run")."""
+    return {"workload": work, "lattices": [f"{p['nx']}x{p['ny']}" for p in params],
+            "sims_per_gpu": len(params),
+            "fluid_nodes_per_step": sum(fluid_nodes(p) for p in params),
+            "physics": "density ratio 10, SRF quadratic law, Gibbs term (seeded synthetic)",
+            "l2": "working set %.0f MB > 129 MB L2; simulations interleaved per step"
+                  % (sum(2 * BYTES_PER_NODE_BUFFER[precision] * p["nx"] * p["ny"]
+                         for p in params) / 1e6)}
+
+
 def run_reference(args) -> None:
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     work = workload(args.workload)
-    # each benchmark step is a bounded sample: one FP64 oracle time step of a
-    # 64x128 channel with the physics of the next member of the workload
+    # each benchmark step advances every lattice of the workload by one FP64
+    # oracle time step on the host cores, as one GPU step advances them all
     from oracle import oracle as orc
     threads = os.cpu_count() or 1
     used = orc.set_threads(threads)
     sims = []
     for p in work:
-        q = dict(p)
-        q.update(nx=64, ny=128, R=12.0, xb=32.0, yb=40.0)
-        o = orc.Oracle(q)
-        o.init_fields(si.bubble_fields(q))
-        sims.append((q, o))
-    for k in range(args.warmup):
-        sims[k % len(sims)][1].step(1)
+        o = orc.Oracle(p)
+        o.init_fields(si.bubble_fields(p))
+        sims.append(o)
+    for _ in range(args.warmup):
+        for o in sims:
+            o.step(1)
     t0 = time.perf_counter()
-    nodes = 0
-    for k in range(args.steps):
-        q, o = sims[k % len(sims)]
-        o.step(1)
-        nodes += fluid_nodes(q)
+    for _ in range(args.steps):
+        for o in sims:
+            o.step(1)
     dt = time.perf_counter() - t0
+    nodes = sum(fluid_nodes(p) for p in work) * args.steps
+    for o in sims:
+        o.close()
     v = nodes / dt / 1e6
     print(json.dumps({
         "impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / max(args.steps, 1) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": "one oracle step of a 64x128 "
-                   "channel per benchmark step, physics of the workload members"},
+        "config": workload_config(args.workload, work, args.precision),
         "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": used, "kind": "oracle",
-                         "sample": "64x128 channel, one FP64 step per benchmark step"},
+                         "sample": f"{args.steps} FP64 time steps of every lattice of the "
+                                   f"workload after {args.warmup} warm-up steps, {dt:.1f} s"},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
 # ---------------------------------------------------------------- GPU arm
+class Batch:
+    """Simulations of one workload on one stream, stepped batched or plain."""
+
+    def __init__(self, lbm, torch, params, precision, stream):
+        self.lbm, self.torch, self.stream = lbm, torch, stream
+        self.params = [dict(p, precision=PRECISION_CODE[precision]) for p in params]
+        self.sims = [lbm.Sim(p, stream=stream, workspace="torch") for p in self.params]
+        for s in self.sims:
+            s.init()                      # analytic initial state, built on the device
+        self.nodes = sum(fluid_nodes(p) for p in self.params)
+        self.tuned_steps = 0
+
+    def tune(self, steps):
+        if steps > 0:
+            self.tuned_steps += self.lbm.lbm_tune_batch(self.sims, steps)
+
+    def launches(self):
+        return sum(s.launches() for s in self.sims)
+
+    def run(self, mode, nsteps, per_step=False, graph=False):
+        if mode == "batched" and not per_step:
+            self.lbm.lbm_step_batch(self.sims, nsteps)  # one call; runs of 64 replay graphs
+        elif mode == "plain" and graph:
+            for s in self.sims:                        # all steps of a sim in one call
+                s.step(nsteps)
+        else:
+            for _ in range(nsteps):
+                if mode == "batched":
+                    self.lbm.lbm_step_batch(self.sims, 1)
+                else:
+                    for s in self.sims:
+                        s.step(1)
+
+    def timed(self, mode, nsteps, barrier, per_step=False, graph=False):
+        """Device time (CUDA events on the sims' stream) of nsteps steps and
+        the kernel launches they issued."""
+        torch = self.torch
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        l0 = self.launches()
+        ev0.record(self.stream)
+        self.run(mode, nsteps, per_step, graph)
+        ev1.record(self.stream)
+        barrier()
+        return ev0.elapsed_time(ev1), self.launches() - l0
+
+    def close(self):
+        for s in self.sims:
+            s.close()
+
+
+def launch_mode(mode, steps, per_step, graph):
+    """How the timed steps were issued: graphs replay only for runs of 64
+    steps in one call."""
+    if mode == "batched":
+        return "batched" + (" graph" if not per_step and steps >= 64 else "")
+    return "plain" + (" graph" if graph and steps >= 64 else "")
+
+
+def sub_measure(lbm, torch, dev_index, params, precision, mode, steps, tune_steps, stream,
+                barrier, graph=True) -> dict:
+    """A device-timed measurement of another workload or storage format, with
+    its clocks: MLUPS and the fraction of the HBM roofline."""
+    b = Batch(lbm, torch, params, precision, stream)
+    if mode == "batched":
+        b.tune(tune_steps)
+        b.run(mode, 64)                   # warm-up that captures the batch graph
+    else:
+        b.run(mode, 64, graph=graph)
+    with ClockSampler(dev_index) as clk:
+        ms, launches = b.timed(mode, steps, barrier, graph=graph)
+    c = clk.summary()
+    value = b.nodes * steps / (ms * 1e-3) / 1e6
+    gbs = value * 1e6 * BYTES_PER_NODE_STEP[precision] / 1e9
+    peak = measured_peaks()["hbm_gbs"]
+    out = {"value": value, "unit": "MLUPS", "storage": precision, "mode": mode,
+           "launch_mode": launch_mode(mode, steps, False, graph),
+           "lattices": sorted({f"{p['nx']}x{p['ny']}" for p in params}),
+           "sims": len(params), "steps": steps, "gpu_launches": launches,
+           "achieved_gbs": gbs, "hbm_frac": gbs / peak,
+           "bytes_per_node_step": BYTES_PER_NODE_STEP[precision],
+           "strip_chunks": sorted(set(lbm.lbm_batch_plan(b.sims)) - {0}),
+           "clocks": {"sm_mhz": c["sm_mhz"], "reasons": c["reasons"]}}
+    b.close()
+    return out
+
+
 def run_gpu(args) -> None:
     import torch
     import torch.distributed as dist
@@ -264,14 +368,9 @@ def run_gpu(args) -> None:
     torch.cuda.set_device(local)
     dev_index = torch.cuda.current_device()
     stream = torch.cuda.Stream()
-    params = workload(args.workload)
-    for p in params:
-        p["precision"] = PRECISION_CODE[args.precision]
-    nodes_per_step = sum(fluid_nodes(p) for p in params)
-
-    sims = [lbm.Sim(p, stream=stream, workspace="torch") for p in params]
-    for s in sims:
-        s.init()                      # analytic initial state, built on the device
+    params = [dict(p, precision=PRECISION_CODE[args.precision]) for p in workload(args.workload)]
+    batch = Batch(lbm, torch, params, args.precision, stream)
+    nodes_per_step = batch.nodes
     torch.cuda.synchronize()
 
     def barrier():
@@ -279,54 +378,26 @@ def run_gpu(args) -> None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def step_all():
-        if args.mode == "batched":
-            lbm.lbm_step_batch(sims, 1)       # one launch over every simulation
-        else:
-            for s in sims:                   # one launch per simulation
-                s.step(1)
-
-    def timed(nsteps):
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        barrier()
-        l0 = sum(s.launches() for s in sims)
-        ev0.record(stream)
-        if args.mode == "batched" and not args.per_step_calls:
-            lbm.lbm_step_batch(sims, nsteps)  # one call: replayed CUDA graphs of 64 steps
-        elif args.graph and args.mode == "plain":
-            for s in sims:                   # all steps in one call: CUDA-graph replay
-                s.step(nsteps)
-        else:
-            for _ in range(nsteps):
-                step_all()
-        ev1.record(stream)
-        barrier()
-        return ev0.elapsed_time(ev1), sum(s.launches() for s in sims) - l0
-
     # measured strip plan of the batched launch (steps outside the timed region)
-    tuned_steps = 0
-    if args.mode == "batched" and args.tune_steps > 0:
-        tuned_steps = lbm.lbm_tune_batch(sims, args.tune_steps)
-    plan = lbm.lbm_batch_plan(sims)
+    if args.mode == "batched":
+        batch.tune(args.tune_steps)
+    plan = lbm.lbm_batch_plan(batch.sims)
     warmup_run = args.warmup
-    if args.mode == "batched" and not args.per_step_calls:
+    if args.mode == "batched" and not args.per_step_calls and args.steps >= 64:
         # at least one 64-step run, so that the batch's graph is captured
         # before the timed region
         warmup_run = max(args.warmup, 64)
-        lbm.lbm_step_batch(sims, warmup_run)
-    else:
-        for _ in range(args.warmup):
-            step_all()
+    batch.run(args.mode, warmup_run, args.per_step_calls, args.graph)
     with ClockSampler(dev_index) as clk:
-        ms, launches = timed(args.steps)
+        ms, launches = batch.timed(args.mode, args.steps, barrier, args.per_step_calls, args.graph)
     clocks = clk.summary()
 
     ms_max = max_over_ranks(ms, "cuda")
     value = weak_scaling_value(ms_max, nodes_per_step, args.steps, ws)
 
-    # roofline of the dominant kernel: every launch in the timed region is the
-    # fused step kernel (one simulation, or the whole batch, per launch)
+    # roofline of the dominant kernel: every launch in the timed region is a
+    # fused step kernel (one simulation, or every simulation of the batch that
+    # the kernel family takes, per launch)
     per_launch_ms = ms / launches
     sims_per_launch = len(params) if args.mode == "batched" else 1
     bpn = BYTES_PER_NODE_STEP[args.precision]
@@ -339,18 +410,36 @@ def run_gpu(args) -> None:
     # the other launch mode on the same simulations, for comparison
     other = None
     if args.compare_modes and len(params) > 1:
-        mode = args.mode
-        args.mode = "plain" if mode == "batched" else "batched"
-        ms_o, _ = timed(max(args.steps // 4, 1))
-        other = {"mode": args.mode,
-                 "value": nodes_per_step * max(args.steps // 4, 1) / (ms_o * 1e-3) / 1e6}
-        args.mode = mode
+        mode = "plain" if args.mode == "batched" else "batched"
+        n_o = max(args.steps // 4, 1)
+        ms_o, _ = batch.timed(mode, n_o, barrier)
+        other = {"mode": mode, "launch_mode": launch_mode(mode, n_o, False, False),
+                 "value": nodes_per_step * n_o / (ms_o * 1e-3) / 1e6}
+    batch.close()
+
+    # sub-results on one GPU: the mixed-precision batched ensemble against the
+    # plain single-simulation path, and the large-lattice precision study
+    extra = {}
+    if ws == 1 and not args.no_extra:
+        plain = sub_measure(lbm, torch, dev_index, [si.channel_256x1024()], "fp32", "plain",
+                            args.extra_steps, 0, stream, barrier)
+        ens = sub_measure(lbm, torch, dev_index, si.ensemble_channels(64, seed=0), "fp16",
+                          "batched", args.extra_steps, args.tune_steps, stream, barrier)
+        extra["mixed_precision"] = {
+            "batched_fp16_ensemble": ens, "plain_fp32_single": plain,
+            "ratio": ens["value"] / plain["value"],
+            "target_ratio": 2.0,
+            "note": "64 channels of uneven size (nx 128..512, multiples of 32; ny = 4 nx) at "
+                    "binary16 storage in one lbm_step_batch call, against lbm_step on one "
+                    "256x1024 FP32 channel"}
+        extra["config3"] = {
+            prec: sub_measure(lbm, torch, dev_index, [si.channel_1024x4096()], prec, "batched",
+                              args.extra_steps, args.tune_steps, stream, barrier)
+            for prec in ("fp32", "fp16", "bf16")}
 
     e2e = run_e2e(args, lbm, torch, stream, params) if not args.no_e2e else None
     served = run_served(args, torch) if (args.serve_requests > 0 and rank == 0) else None
 
-    for s in sims:
-        s.close()
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
@@ -360,22 +449,19 @@ def run_gpu(args) -> None:
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "lattices": [f"{p['nx']}x{p['ny']}" for p in params],
-                       "sims_per_gpu": len(params), "fluid_nodes_per_step": nodes_per_step,
-                       "launch_mode": args.mode + (" graph" if (args.graph and args.mode == "plain") or
-                                                   (args.mode == "batched" and not args.per_step_calls)
-                                                   else ""),
-                       "warmup_steps_run": warmup_run,
-                       "other_mode": other,
-                       "strip_plan": {"tuned": tuned_steps > 0, "tuning_steps": tuned_steps,
-                                      "strip_chunks": sorted(set(plan) - {0})},
-                       "storage": args.precision,
-                       "l2": "working set %.0f MB > 129 MB L2; simulations interleaved per step"
-                             % (sum(2 * BYTES_PER_NODE_BUFFER[args.precision] * p["nx"] * p["ny"]
-                                    for p in params) / 1e6),
-                       "parallelism": f"replicas x{ws}"},
+            "config": workload_config(args.workload, params, args.precision),
+            "run": {"storage": args.precision,
+                    "launch_mode": launch_mode(args.mode, args.steps, args.per_step_calls,
+                                               args.graph),
+                    "warmup_steps_run": warmup_run,
+                    "other_mode": other,
+                    "strip_plan": {"tuned": batch.tuned_steps > 0,
+                                   "tuning_steps": batch.tuned_steps,
+                                   "strip_chunks": sorted(set(plan) - {0})},
+                    "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                         "frac_of_nominal_8tbs": achieved / 8000.0,
                          "traffic": traffic, "peak_source": peaks["source"],
                          "kernel": kernel, "bytes_per_node_step": bpn},
             "cpu_baseline": cpu,
@@ -385,6 +471,7 @@ def run_gpu(args) -> None:
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                        "reasons": clocks["reasons"]},
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -438,13 +525,13 @@ def run_e2e(args, lbm, torch, stream, params) -> dict:
             for _ in range(n):            # interleaved, as in the device-timed loop
                 for s in sims:
                     s.step(1)
-        for s in sims:
-            s.observe()
-            d2h += 8 * 8
+        lbm.lbm_observe_enqueue(sims)     # every sim's observables, one wait
+        lbm.lbm_observe_collect(sims)
+        d2h += 13 * 8 * len(sims)
         done += n
     for s, out in zip(sims, host_out):
         lbm.lbm_observe(s.handle, out)
-        d2h += out.size * 4 + 8 * 8
+        d2h += out.size * 4 + 13 * 8
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     for s in sims:
@@ -480,6 +567,10 @@ def main():
                     help="batched mode: steps per candidate strip plan for lbm_tune_batch "
                          "before the warm-up (0: the cost model's plan)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
+    ap.add_argument("--extra-steps", type=int, default=200,
+                    help="timed steps of each sub-result (mixed_precision, config3)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the mixed_precision and config3 sub-results")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=48,

@@ -55,15 +55,16 @@ typedef enum {
  * in exact arithmetic).
  *   LBM_FP32: the 36 populations of each node in FP32 (144 B per node and
  *     buffer).
- *   LBM_FP16, LBM_BF16: per node, the FP32 zeroth moments M = (M_f, M_g, M_h,
- *     M_q) of the populations it pushed at the last step (16 B), and per
- *     population its deviation from w_a M of the node that pushed it (the
- *     source y - e_a, or the node itself for a population that bounced back),
- *     stored in IEEE binary16 or bfloat16 (72 B per node and buffer).  The
- *     rest part carries the conserved scalars phi, T, psi in FP32; the
- *     rounding errors of the nine deviations a node pushes are folded into its
- *     M, so the populations it pushes sum to their FP32 values.  Populations
- *     at the API (lbm_init, lbm_get_populations) stay FP32 arrays. */
+ *   LBM_FP16, LBM_BF16: per node, m = M/36 in FP32 for the zeroth moments
+ *     M = (M_f, M_g, M_h, M_q) of the populations it pushed at the last step
+ *     (16 B), and per population its deviation from k_a m of the node that
+ *     pushed it (the source y - e_a, or the node itself for a population that
+ *     bounced back), stored in IEEE binary16 or bfloat16 (72 B per node and
+ *     buffer); k_a = 36 w_a = 16, 4, 1 are exact integer weights.  The rest
+ *     part carries the conserved scalars phi, T, psi in FP32; the rounding
+ *     errors of the nine deviations a node pushes are folded into its m, so
+ *     the populations it pushes sum to their FP32 values.  Populations at the
+ *     API (lbm_init, lbm_get_populations) stay FP32 arrays. */
 enum { LBM_FP32 = 0, LBM_FP16 = 1, LBM_BF16 = 2 };
 
 /* Problem parameters, named as in the paper's problem statement (Sec. 2,
@@ -172,19 +173,23 @@ lbm_status lbm_create_ex(const lbm_params* p, void* stream, void* workspace,
  * Errors: LBM_EINVAL (NULL sim), LBM_ECUDA. */
 lbm_status lbm_init(lbm_sim* sim, const double* fields, const float* populations);
 
-/* Advances nsteps time steps: each is one launch of the fused kernel that
- * streams the populations (Eqs. (27)-(28), (33)-(34), (38)-(39), (43)-(44)
- * streaming steps), builds phi, T, psi, p* and the forces on a shared-memory
- * tile with a two-node halo, and collides f, g, h, q.  Asynchronous on the
- * sim's stream; long runs replay a captured CUDA graph.  nsteps = 0 is a
- * no-op.  Errors: LBM_EINVAL (nsteps < 0), LBM_ESTATE (not initialised),
- * LBM_ECUDA. */
+/* Advances nsteps time steps: each is one launch of a fused kernel that
+ * reads the populations, builds phi, T, psi, p* and the forces of Sec. 3 and
+ * App. C from them with the isotropic stencils (a two-node halo), collides f,
+ * g, h, q (App. B-E) and streams the results to the neighbours (Eqs. (27)-(28),
+ * (33)-(34), (38)-(39), (43)-(44)).  Lattices with nx >= 32, nx a multiple of
+ * 4 (FP32) or 8 (16-bit storage), at least 16 fluid rows and walls (or, FP32,
+ * a periodic y axis of whole 8-row chunks) take the streaming kernels (see
+ * lbm_batch_plan); the others a tile kernel.  Asynchronous on the sim's
+ * stream; long runs replay a captured CUDA graph.  nsteps = 0 is a no-op.
+ * Errors: LBM_EINVAL (nsteps < 0), LBM_ESTATE (not initialised), LBM_ECUDA. */
 lbm_status lbm_step(lbm_sim* sim, int64_t nsteps);
 
 /* Advances n simulations (1 <= n <= 64) by nsteps time steps with one kernel
- * launch per step and storage precision covering the tiles of all the sims
- * of that precision; the simulations may differ in size, parameters and
- * precision.  Each step is the same fused update as
+ * launch per step and kernel family: the streaming kernel of each storage
+ * precision (at most 48 16-bit sims per launch) and the tile kernel of each
+ * precision, each launch covering all the sims it takes; the simulations may
+ * differ in size, parameters and precision.  Each step is the same fused update as
  * lbm_step, so the result of every simulation equals what lbm_step gives it
  * alone.  All sims must be initialised, distinct, and created on the same
  * device and stream; the launches are issued on that stream (asynchronous)
@@ -195,13 +200,13 @@ lbm_status lbm_step(lbm_sim* sim, int64_t nsteps);
  * LBM_ECUDA. */
 lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps);
 
-/* Strip plan of a batch.  FP32 sims with walls, nx a multiple of 32 and at
- * least 16 fluid rows are stepped by the streaming kernel: one block walks a
- * 32-wide column over a strip of chunks of 8 rows.  strip_chunks[i] (caller's
- * array of n) receives the strip length, in chunks, that lbm_step_batch uses
- * for sims[i] in this batch (0 for sims stepped by the tile kernel).  Without
- * tuning it comes from a cost model of the launch (one strip per block slot,
- * 2 x SMs slots, longest first).  Host only; arguments as lbm_step_batch.  The
+/* Strip plan of a batch.  Sims eligible for the streaming kernels (see
+ * lbm_step) are stepped by blocks that each walk one column of up to 32
+ * nodes over a strip of chunks of 8 rows.  strip_chunks[i] (caller's array of
+ * n) receives the strip length, in chunks, that lbm_step_batch uses for
+ * sims[i] in this batch (0 for sims stepped by a tile kernel).  Without
+ * tuning it comes from a cost model of each streaming launch (one strip per
+ * block slot, resident blocks x SMs slots, longest first).  Host only; arguments as lbm_step_batch.  The
  * paper has no counterpart (it fixes no GPU work decomposition).  Errors:
  * LBM_EINVAL, LBM_ESTATE. */
 lbm_status lbm_batch_plan(lbm_sim* const* sims, int32_t n, int32_t* strip_chunks);
@@ -229,10 +234,27 @@ lbm_status lbm_tune_batch(lbm_sim* const* sims, int32_t n, int32_t trial_steps,
  * value was found (out and host_fields are still written). */
 lbm_status lbm_observe(lbm_sim* sim, lbm_obs* out, double* host_fields);
 
+/* Observables of several simulations with one wait, for serving loops that
+ * keep the GPU busy while they read results.  lbm_observe_enqueue enqueues,
+ * for each of sims[0..n-1] (1 <= n <= 64; distinct, initialised, one device
+ * and stream, as lbm_step_batch), the evaluation lbm_observe performs -- the
+ * fields of the current state, the FP64 reductions, and the copy of their
+ * result into the sim's pinned host buffer -- and returns without waiting;
+ * later work on the stream (further steps) does not change the result.
+ * lbm_observe_collect waits for those evaluations and writes out[i] (caller's
+ * array of n) for sims[i], with t the step count at enqueue time; status
+ * (caller's array of n, may be NULL) receives each sim's lbm_observe status
+ * (LBM_OK, LBM_EUNSTABLE, LBM_ETIMEOUT).  A second enqueue before the collect
+ * replaces the first.  The paper has no counterpart.
+ * Errors: LBM_EINVAL, LBM_ESTATE (collect without an enqueued evaluation),
+ * LBM_ECUDA. */
+lbm_status lbm_observe_enqueue(lbm_sim* const* sims, int32_t n);
+lbm_status lbm_observe_collect(lbm_sim* const* sims, int32_t n, lbm_obs* out, int32_t* status);
+
 /* Copies the current post-streaming populations into the host float array
  * [4][9][ny][nx] (the layout lbm_init accepts back: checkpoint/restart; wall
  * rows hold 0).  16-bit storage: the populations are rebuilt as
- * w_a M(source) + deviation in FP32.  Synchronises the stream.  Errors:
+ * k_a m(source) + deviation in FP32.  Synchronises the stream.  Errors:
  * LBM_ESTATE, LBM_ECUDA. */
 lbm_status lbm_get_populations(lbm_sim* sim, float* host_pops);
 

@@ -218,10 +218,14 @@ struct lbm_sim {
     double* h_res;   // pinned, 16 doubles
     int* err;        // device flag: a bounded wait in a kernel gave up
     bool have_tmap;  // TMA descriptors of both population buffers are valid
-    CUtensorMap tmap[2];
-    bool ystream;    // steps use the y-streaming kernel (stream_eligible, TMA side maps)
-    CUtensorMap tside[2];
+    CUtensorMap tmap[2];   // populations (FP32) or deviations (16-bit), box {kTileX, 8, 36}
+    bool ystream;    // steps use a streaming kernel (stream_eligible, descriptors valid)
+    CUtensorMap tside[2];  // side columns: box {4, 8, 36} (FP32) or {8, 8, 36} (16-bit)
+    CUtensorMap tmom[2];   // 16-bit storage: rest-state moments, box {4, 8, 10}
     int strip_chunks;  // chunks per strip when stepped alone
+    cudaEvent_t obs_event;  // recorded after the last enqueued observation's copy
+    bool obs_pending;       // an observation was enqueued (h_res is or will be valid)
+    int64_t obs_t;          // the step count it observes
     int num_sms;
     uint64_t id;       // unique over the process, never reused
 };
@@ -233,13 +237,17 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// TMA descriptors of the population tensors [36][ny][nx] (FP32), box
-// {kTileX, kTileY, 36}.  TMA needs 16-byte row strides, i.e. nx % 4 == 0;
-// otherwise (or if the driver lacks the entry point) every tile is staged
-// with per-thread loads instead.
+// TMA descriptors of both population buffers.  FP32: the populations
+// [36][ny][nx], box {kTileX, 8, 36} (tile and streaming kernels) and the
+// streaming kernel's side box {4, 8, 36}; TMA needs 16-byte row strides,
+// nx % 4 == 0.  16-bit storage: the deviations [36][ny][nx] (boxes {kTileX, 8,
+// 36} and {8, 8, 36}; nx % 8 == 0) and the rest-state moments, the float4
+// array [ny][nx] viewed as [ny][nx][4] floats (box {4, 8, 10}).  Without
+// them every step takes the tile kernels, which stage with plain loads.
 bool encode_population_maps(lbm_sim* s)
 {
-    if (s->p.nx % 4 != 0) return false;
+    const bool fp32 = s->p.precision == LBM_FP32;
+    if (s->p.nx % (fp32 ? 4 : 8) != 0) return false;
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
@@ -247,27 +255,39 @@ bool encode_population_maps(lbm_sim* s)
         q != cudaDriverEntryPointSuccess || !fn)
         return false;
     EncodeTiledFn encode = reinterpret_cast<EncodeTiledFn>(fn);
+    const cuuint64_t esz = fp32 ? sizeof(float) : 2;
+    const CUtensorMapDataType dt = fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     const cuuint64_t dims[3] = {(cuuint64_t)s->p.nx, (cuuint64_t)s->p.ny, 36};
-    const cuuint64_t strides[2] = {(cuuint64_t)s->p.nx * sizeof(float),
-                                   (cuuint64_t)s->p.nx * s->p.ny * sizeof(float)};
+    const cuuint64_t strides[2] = {(cuuint64_t)s->p.nx * esz, (cuuint64_t)s->p.nx * s->p.ny * esz};
     const cuuint32_t box[3] = {(cuuint32_t)kTileX, (cuuint32_t)kTileY, 36};
     const cuuint32_t estride[3] = {1, 1, 1};
-    const cuuint32_t side_box[3] = {4, (cuuint32_t)kTileY, 36};
+    const cuuint32_t side_box[3] = {fp32 ? 4u : 8u, (cuuint32_t)kTileY, 36};
+    const cuuint64_t mdims[3] = {4, (cuuint64_t)s->p.nx, (cuuint64_t)s->p.ny};
+    const cuuint64_t mstrides[2] = {4 * sizeof(float), (cuuint64_t)s->p.nx * 4 * sizeof(float)};
+    const cuuint32_t mbox[3] = {4, 8, (cuuint32_t)kTileY + 2};
     for (int b = 0; b < 2; ++b) {
-        CUresult r = encode(&s->tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->pop[b], dims, strides,
-                            box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        CUresult r = encode(&s->tmap[b], dt, 3, s->pop[b], dims, strides, box, estride,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return false;
-        // side boxes of the streaming kernel: four columns on either side
-        r = encode(&s->tside[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->pop[b], dims, strides,
-                   side_box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        r = encode(&s->tside[b], dt, 3, s->pop[b], dims, strides, side_box, estride,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+        if (fp32) continue;
+        r = encode(&s->tmom[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->mom[b], mdims, mstrides,
+                   mbox, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return false;
     }
     return true;
 }
 
-const CUtensorMap* map_of(const lbm_sim* s, int buf) { return s->have_tmap ? &s->tmap[buf] : nullptr; }
+// The FP32 tile kernels' descriptor of buffer buf, if any.
+const CUtensorMap* map_of(const lbm_sim* s, int buf)
+{
+    return s->have_tmap && s->p.precision == LBM_FP32 ? &s->tmap[buf] : nullptr;
+}
 
 // Strip lengths for one streaming launch over n lattices (plan[i]: chunks of
 // 8 rows per strip of lattice i).  The candidates are target lengths L; a
@@ -295,7 +315,7 @@ void plan_for_length(const int* nch, int n, int L, int* plan)
 
 // The model: a strip of L chunks costs about L + 2 chunk-times (the chunk
 // below it is read first, plus start-up); strips run on the streaming
-// kernel's resident block slots (stream_blocks_per_sm() x num_sms) in launch
+// kernel's resident block slots (stream_blocks_per_sm x num_sms) in launch
 // order, longest first, a slot taking the next strip when it frees.  Returns
 // the predicted launch time in chunk-times.
 double predicted_span(const int* nch, const int* ncol, int n, const int* plan, int slots)
@@ -323,7 +343,7 @@ double predicted_span(const int* nch, const int* ncol, int n, const int* plan, i
 // order), since lbm_step_batch may be called once per step.  A plan measured
 // by lbm_tune_batch (tuned) replaces the model's and is evicted last.
 struct PlanEntry {
-    int n = -1, sms = 0;
+    int n = -1, sms = 0, precision = 0;
     bool tuned = false;
     int nchunks[kMaxBatch], ncol[kMaxBatch], plan[kMaxBatch];
 };
@@ -339,10 +359,10 @@ void plan_key(const LbmDev* const* devs, int n, int* nch, int* ncol)
     }
 }
 
-PlanEntry* find_plan(const int* nch, const int* ncol, int n, int sms)
+PlanEntry* find_plan(const int* nch, const int* ncol, int n, int sms, int precision)
 {
     for (PlanEntry& e : plan_cache) {
-        if (e.n != n || e.sms != sms) continue;
+        if (e.n != n || e.sms != sms || e.precision != precision) continue;
         bool same = true;
         for (int i = 0; i < n && same; ++i) same = e.nchunks[i] == nch[i] && e.ncol[i] == ncol[i];
         if (same) return &e;
@@ -350,9 +370,10 @@ PlanEntry* find_plan(const int* nch, const int* ncol, int n, int sms)
     return nullptr;
 }
 
-void store_plan(const int* nch, const int* ncol, int n, int sms, const int* plan, bool tuned)
+void store_plan(const int* nch, const int* ncol, int n, int sms, int precision, const int* plan,
+                bool tuned)
 {
-    PlanEntry* e = find_plan(nch, ncol, n, sms);
+    PlanEntry* e = find_plan(nch, ncol, n, sms, precision);
     if (!e) {
         // round robin, passing over tuned entries while an untuned one is left
         for (int k = 0; k < kPlanCache && !e; ++k) {
@@ -369,6 +390,7 @@ void store_plan(const int* nch, const int* ncol, int n, int sms, const int* plan
     }
     e->n = n;
     e->sms = sms;
+    e->precision = precision;
     e->tuned = tuned;
     std::memcpy(e->nchunks, nch, sizeof(int) * n);
     std::memcpy(e->ncol, ncol, sizeof(int) * n);
@@ -383,16 +405,16 @@ void store_plan(const int* nch, const int* ncol, int n, int sms, const int* plan
 // neighbouring columns run at other times) than they save in start-up.
 constexpr int kMultiWaveMaxStrip = 16;
 
-void plan_strips(const LbmDev* const* devs, int n, int num_sms, int* out)
+void plan_strips(const LbmDev* const* devs, int n, int num_sms, int precision, int* out)
 {
     int nch[kMaxBatch], ncol[kMaxBatch];
     plan_key(devs, n, nch, ncol);
-    if (const PlanEntry* e = find_plan(nch, ncol, n, num_sms)) {
+    if (const PlanEntry* e = find_plan(nch, ncol, n, num_sms, precision)) {
         std::memcpy(out, e->plan, sizeof(int) * n);
         return;
     }
     const int maxch = std::max(1, *std::max_element(nch, nch + n));
-    const int slots = stream_blocks_per_sm() * std::max(num_sms, 1);
+    const int slots = stream_blocks_per_sm(precision) * std::max(num_sms, 1);
     long long cols = 0;
     for (int i = 0; i < n; ++i) cols += ncol[i];
     const bool multi_wave = cols > slots;
@@ -407,7 +429,7 @@ void plan_strips(const LbmDev* const* devs, int n, int num_sms, int* out)
             std::memcpy(best_plan, plan, sizeof(int) * n);
         }
     }
-    store_plan(nch, ncol, n, num_sms, best_plan, false);
+    store_plan(nch, ncol, n, num_sms, precision, best_plan, false);
     std::memcpy(out, best_plan, sizeof(int) * n);
 }
 
@@ -462,8 +484,8 @@ static lbm_status create_impl(const lbm_params* p, void* stream, void* ws, size_
     s->part = reinterpret_cast<double*>(base + 2 * L.pop_bytes + L.fld_bytes);
     s->res = reinterpret_cast<double*>(base + 2 * L.pop_bytes + L.fld_bytes + L.part_bytes);
     s->err = reinterpret_cast<int*>(s->res + 12);
-    s->have_tmap = p->precision == LBM_FP32 && encode_population_maps(s);
-    s->ystream = s->have_tmap && stream_eligible(s->dev);
+    s->have_tmap = encode_population_maps(s);
+    s->ystream = s->have_tmap && stream_eligible(s->dev, p->precision);
     e = p->precision == LBM_FP32 ? cudaSuccess : prepare_dev_storage(p->precision);
     if (e == cudaSuccess && s->ystream) {
         int sms = 0;
@@ -471,10 +493,11 @@ static lbm_status create_impl(const lbm_params* p, void* stream, void* ws, size_
         if (e == cudaSuccess) e = prepare_stream();
         s->num_sms = sms > 0 ? sms : 1;
         const LbmDev* one = &s->dev;
-        plan_strips(&one, 1, s->num_sms, &s->strip_chunks);
+        plan_strips(&one, 1, s->num_sms, p->precision, &s->strip_chunks);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s->h_res), 16 * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->obs_event, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         lbm_destroy(s);
         return fail(LBM_ECUDA, "stream/pinned setup: %s", cudaGetErrorString(e));
@@ -520,6 +543,7 @@ void lbm_destroy(lbm_sim* s)
     if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
     if (s->graph) cudaGraphDestroy(s->graph);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->obs_event) cudaEventDestroy(s->obs_event);
     if (s->h_stage) cudaFreeHost(s->h_stage);
     if (s->h_res) cudaFreeHost(s->h_res);
     if (s->owns_ws && s->ws) cudaFree(s->ws);
@@ -573,15 +597,47 @@ static void stream_entry(StreamBatchArgs& a, int i, const lbm_sim* s, int from, 
     a.first[i + 1] = a.first[i] + stream_blocks(s->dev, strip_chunks);
 }
 
+static void stream16_entry(Stream16Args& a, int i, const lbm_sim* s, int from, int strip_chunks)
+{
+    a.tmap[i] = s->tmap[from];
+    a.tside[i] = s->tside[from];
+    a.tmom[i] = s->tmom[from];
+    a.dev[i] = s->dev;
+    a.dst[i] = s->pop[from ^ 1];
+    a.mdst[i] = s->mom[from ^ 1];
+    a.err[i] = s->err;
+    a.strip_chunks[i] = strip_chunks;
+    a.first[i + 1] = a.first[i] + stream_blocks(s->dev, strip_chunks);
+}
+
+// One streaming launch over sims[0 .. n-1] (one storage precision), each
+// from its current buffer with strip lengths plan[].
+static cudaError_t launch_stream_group(lbm_sim* const* sims, int n, const int* plan, cudaStream_t st)
+{
+    static thread_local StreamBatchArgs a32;  // ~27 KB each: kept off the stack
+    static thread_local Stream16Args a16;
+    const int precision = sims[0]->p.precision;
+    if (precision == LBM_FP32) {
+        a32.n = n;
+        a32.first[0] = 0;
+        for (int i = 0; i < n; ++i) stream_entry(a32, i, sims[i], sims[i]->cur, plan[i]);
+        return launch_stream_batch(a32, st);
+    }
+    a16.n = n;
+    a16.first[0] = 0;
+    for (int i = 0; i < n; ++i) stream16_entry(a16, i, sims[i], sims[i]->cur, plan[i]);
+    return launch_stream16_batch(a16, precision, st);
+}
+
 // One step from buffer `from` to the other one, on stream st.
 static cudaError_t step_once(lbm_sim* s, int from, cudaStream_t st)
 {
     if (s->ystream) {
-        static thread_local StreamBatchArgs a;   // 26 KB: kept off the stack
-        a.n = 1;
-        a.first[0] = 0;
-        stream_entry(a, 0, s, from, s->strip_chunks);
-        return launch_stream_batch(a, st);
+        const int cur = s->cur;
+        s->cur = from;
+        cudaError_t e = launch_stream_group(&s, 1, &s->strip_chunks, st);
+        s->cur = cur;
+        return e;
     }
     if (s->p.precision == LBM_FP32)
         return launch_step(s->dev, static_cast<const float*>(s->pop[from]),
@@ -606,8 +662,8 @@ static size_t pop_buffer_bytes(const lbm_sim* s)
     return s->p.precision == LBM_FP32 ? 36 * N * sizeof(float) : layout_of(&s->p).pop_bytes;
 }
 
-// 16-bit storage from host FP32 populations: M of every node = the sums of its
-// own nine populations per set (FP64, rounded once), then the deviations,
+// 16-bit storage from host FP32 populations: m of every node = the sums of its
+// own nine populations per set over 36 (FP64, rounded once), then the deviations,
 // six planes at a time through the field buffer, their rounding errors
 // gathered in the other buffer's M and folded into M.
 static lbm_status split_host_populations(lbm_sim* s, const float* populations)
@@ -621,7 +677,7 @@ static lbm_status split_host_populations(lbm_sim* s, const float* populations)
         for (int set = 0; set < 4; ++set) {
             double acc = 0.0;
             for (int a = 0; a < 9; ++a) acc += populations[(size_t)(9 * set + a) * N + o];
-            s->h_stage[4 * o + set] = (float)acc;
+            s->h_stage[4 * o + set] = (float)(acc / 36.0);
         }
     CUDA_TRY(cudaMemcpyAsync(s->mom[0], s->h_stage, 4 * N * sizeof(float), cudaMemcpyHostToDevice,
                              s->stream));
@@ -760,19 +816,52 @@ static lbm_status check_batch(lbm_sim* const* sims, int32_t n, const char* who)
     return LBM_OK;
 }
 
-// The streaming sims of a batch, in argument order, and their planned strip
-// lengths (plan[k] for stream[k]).
-static int stream_group(lbm_sim* const* sims, int n, lbm_sim** stream, int* plan)
+// The streaming launches of a batch: its streaming sims grouped by storage
+// precision (FP32, then binary16, then bfloat16; at most kMaxBatch16 16-bit
+// sims per launch), each group in argument order with its planned strip
+// lengths.  pos[] maps every streaming sim, in argument order, to its slot in
+// the concatenated member lists.
+struct StreamLaunches {
+    int count = 0;            // launches
+    int sn = 0;               // streaming sims
+    int begin[2 * kMaxBatch + 1];
+    lbm_sim* sims[kMaxBatch]; // members, launch after launch
+    int plan[kMaxBatch];      // strip chunks of each member
+    int pos[kMaxBatch];       // argument-order streaming sim -> member slot
+};
+
+static void stream_launches(lbm_sim* const* sims, int n, StreamLaunches& L)
 {
-    int sn = 0;
-    for (int i = 0; i < n; ++i)
-        if (sims[i]->ystream) stream[sn++] = sims[i];
-    if (sn > 0) {
-        const LbmDev* devs[kMaxBatch];
-        for (int i = 0; i < sn; ++i) devs[i] = &stream[i]->dev;
-        plan_strips(devs, sn, stream[0]->num_sms, plan);
+    L.count = 0;
+    L.sn = 0;
+    L.begin[0] = 0;
+    int slot = 0;
+    int argpos[kMaxBatch];
+    int nstream = 0;
+    for (int i = 0; i < n; ++i) argpos[i] = sims[i]->ystream ? nstream++ : -1;
+    L.sn = nstream;
+    for (int prec = LBM_FP32; prec <= LBM_BF16; ++prec) {
+        const int cap = prec == LBM_FP32 ? kMaxBatch : kMaxBatch16;
+        int in_launch = 0;
+        for (int i = 0; i < n; ++i) {
+            if (!sims[i]->ystream || sims[i]->p.precision != prec) continue;
+            if (in_launch == cap) {
+                L.begin[++L.count] = slot;
+                in_launch = 0;
+            }
+            L.sims[slot] = sims[i];
+            L.pos[argpos[i]] = slot;
+            ++slot;
+            ++in_launch;
+        }
+        if (in_launch > 0) L.begin[++L.count] = slot;
     }
-    return sn;
+    for (int g = 0; g < L.count; ++g) {
+        const int b = L.begin[g], m = L.begin[g + 1] - b;
+        const LbmDev* devs[kMaxBatch];
+        for (int i = 0; i < m; ++i) devs[i] = &L.sims[b + i]->dev;
+        plan_strips(devs, m, L.sims[b]->num_sms, L.sims[b]->p.precision, L.plan + b);
+    }
 }
 
 // Captured CUDA graphs of kGraphSteps batched steps, per host thread, keyed
@@ -803,28 +892,28 @@ static BatchGraph* find_batch_graph(lbm_sim* const* sims, int n, const int* plan
 }
 
 // nsteps batched steps; forced (optional) replaces the planned strip lengths
-// of the streaming group (one per streaming sim, in argument order).  Runs of
+// of the streaming sims (one per streaming sim, in argument order).  Runs of
 // kGraphSteps steps with the planned strips replay a captured graph.
 static lbm_status step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps, const int* forced)
 {
-    // one launch per kernel family present: the streaming kernel for the
-    // FP32 sims it takes, the tile kernel per storage precision for the rest
+    // one launch per streaming group (stream_launches), and one tile-kernel
+    // launch per storage precision for the rest
     static thread_local BatchArgs args[3];  // 20 KB each: kept off the stack
-    static thread_local StreamBatchArgs sargs;
+    static thread_local StreamLaunches SL;
+    static thread_local int sorted_plan[kMaxBatch];
+    static thread_local lbm_sim* sorted_sims[kMaxBatch];
     int tiles[3] = {0, 0, 0};
     lbm_sim* group[3][kMaxBatch];
-    lbm_sim* sgroup[kMaxBatch];
     for (int k = 0; k < 3; ++k) {
         args[k].n = 0;
         args[k].first[0] = 0;
     }
-    int schunks[kMaxBatch];
-    const int sn = stream_group(sims, n, sgroup, schunks);
-    if (forced) std::memcpy(schunks, forced, sizeof(int) * sn);
-    const int plan_key_chunks = sn;
+    stream_launches(sims, n, SL);
+    if (forced)
+        for (int i = 0; i < SL.sn; ++i) SL.plan[SL.pos[i]] = forced[i];
     int plan_in_arg_order[kMaxBatch];
-    std::memcpy(plan_in_arg_order, schunks, sizeof(int) * sn);
-    int kernels = sn > 0 ? 1 : 0;   // launches per step
+    for (int i = 0; i < SL.sn; ++i) plan_in_arg_order[i] = SL.plan[SL.pos[i]];
+    int kernels = SL.count;   // launches per step
     for (int i = 0; i < n; ++i) {
         if (sims[i]->ystream) continue;
         const int k = sims[i]->p.precision;
@@ -837,20 +926,26 @@ static lbm_status step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps, co
         tiles[k] = a.first[a.n + 1];
         a.n += 1;
     }
-    // longest strips first: blocks start in index order, so the short ones
-    // fill the tail of the launch
-    for (int i = 1; i < sn; ++i)
-        for (int j = i; j > 0 && schunks[j] > schunks[j - 1]; --j) {
-            std::swap(schunks[j], schunks[j - 1]);
-            std::swap(sgroup[j], sgroup[j - 1]);
+    // within a launch, longest strips first: blocks start in index order, so
+    // the short ones fill the tail of the launch
+    for (int g = 0; g < SL.count; ++g) {
+        const int b = SL.begin[g], m = SL.begin[g + 1] - b;
+        for (int i = 0; i < m; ++i) {
+            sorted_sims[b + i] = SL.sims[b + i];
+            sorted_plan[b + i] = SL.plan[b + i];
         }
+        for (int i = 1; i < m; ++i)
+            for (int j = b + i; j > b && sorted_plan[j] > sorted_plan[j - 1]; --j) {
+                std::swap(sorted_plan[j], sorted_plan[j - 1]);
+                std::swap(sorted_sims[j], sorted_sims[j - 1]);
+            }
+    }
     // the kernels of one step from each sim's current buffer; flips the buffers
     auto one_step = [&](cudaStream_t st) -> cudaError_t {
-        if (sn > 0) {
-            sargs.n = sn;
-            sargs.first[0] = 0;
-            for (int i = 0; i < sn; ++i) stream_entry(sargs, i, sgroup[i], sgroup[i]->cur, schunks[i]);
-            cudaError_t e = launch_stream_batch(sargs, st);
+        for (int g = 0; g < SL.count; ++g) {
+            const int b = SL.begin[g];
+            cudaError_t e = launch_stream_group(sorted_sims + b, SL.begin[g + 1] - b,
+                                                sorted_plan + b, st);
             if (e != cudaSuccess) return e;
         }
         for (int k = 0; k < 3; ++k) {
@@ -862,8 +957,9 @@ static lbm_status step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps, co
                 a.dst[i] = s->pop[s->cur ^ 1];
                 a.msrc[i] = s->mom[s->cur];
                 a.mdst[i] = s->mom[s->cur ^ 1];
-                a.has_tmap[i] = s->have_tmap ? 1 : 0;
-                if (s->have_tmap) a.tmap[i] = s->tmap[s->cur];
+                const CUtensorMap* m = map_of(s, s->cur);
+                a.has_tmap[i] = m ? 1 : 0;
+                if (m) a.tmap[i] = *m;
             }
             cudaError_t e = k == LBM_FP32 ? launch_step_batch(a, tiles[k], st)
                                           : launch_step_batch_dev(a, k, tiles[k], st);
@@ -874,7 +970,7 @@ static lbm_status step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps, co
     };
     int64_t left = nsteps;
     if (!forced && left >= kGraphSteps) {
-        BatchGraph* g = find_batch_graph(sims, n, plan_in_arg_order, plan_key_chunks);
+        BatchGraph* g = find_batch_graph(sims, n, plan_in_arg_order, SL.sn);
         if (!g) {
             int cur0[kMaxBatch];
             for (int i = 0; i < n; ++i) cur0[i] = sims[i]->cur;
@@ -894,12 +990,12 @@ static lbm_status step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps, co
             batch_graph_next = (batch_graph_next + 1) % kBatchGraphs;
             if (g->exec) cudaGraphExecDestroy(g->exec);
             g->n = n;
-            g->sn = plan_key_chunks;
+            g->sn = SL.sn;
             for (int i = 0; i < n; ++i) {
                 g->id[i] = sims[i]->id;
                 g->cur[i] = cur0[i];
             }
-            std::memcpy(g->plan, plan_in_arg_order, sizeof(int) * plan_key_chunks);
+            std::memcpy(g->plan, plan_in_arg_order, sizeof(int) * SL.sn);
             g->stream = sims[0]->stream;
             g->exec = exec;
         }
@@ -933,10 +1029,9 @@ lbm_status lbm_batch_plan(lbm_sim* const* sims, int32_t n, int32_t* strip_chunks
     if (!strip_chunks) return fail(LBM_EINVAL, "strip_chunks is NULL");
     lbm_status st = check_batch(sims, n, "lbm_batch_plan");
     if (st != LBM_OK) return st;
-    lbm_sim* sg[kMaxBatch];
-    int plan[kMaxBatch];
-    stream_group(sims, n, sg, plan);
-    for (int i = 0, k = 0; i < n; ++i) strip_chunks[i] = sims[i]->ystream ? plan[k++] : 0;
+    static thread_local StreamLaunches SL;
+    stream_launches(sims, n, SL);
+    for (int i = 0, k = 0; i < n; ++i) strip_chunks[i] = sims[i]->ystream ? SL.plan[SL.pos[k++]] : 0;
     return LBM_OK;
 }
 
@@ -947,65 +1042,121 @@ lbm_status lbm_tune_batch(lbm_sim* const* sims, int32_t n, int32_t trial_steps, 
     lbm_status st = check_batch(sims, n, "lbm_tune_batch");
     if (st != LBM_OK) return st;
     if (trial_steps < 1) return fail(LBM_EINVAL, "trial_steps must be >= 1 (got %d)", trial_steps);
-    lbm_sim* sg[kMaxBatch];
-    int model[kMaxBatch];
-    const int sn = stream_group(sims, n, sg, model);
-    if (sn == 0) return LBM_OK;            // no streaming lattice: nothing to plan
-    int nch[kMaxBatch], ncol[kMaxBatch];
-    const LbmDev* devs[kMaxBatch];
-    for (int i = 0; i < sn; ++i) devs[i] = &sg[i]->dev;
-    plan_key(devs, sn, nch, ncol);
-    // distinct plans of the candidate lengths, the model's first
-    std::vector<std::vector<int>> plans{std::vector<int>(model, model + sn)};
-    std::vector<int> plan(sn);
-    for (int L : candidate_lengths(*std::max_element(nch, nch + sn))) {
-        plan_for_length(nch, sn, L, plan.data());
-        if (std::find(plans.begin(), plans.end(), plan) == plans.end()) plans.push_back(plan);
-    }
+    static thread_local StreamLaunches SL;
+    stream_launches(sims, n, SL);
+    if (SL.sn == 0) return LBM_OK;            // no streaming lattice: nothing to plan
+    // the plan of every streaming sim in argument order; each launch group is
+    // tuned in turn with the others at their best plan so far
+    std::vector<int> arg_plan(SL.sn);
+    for (int i = 0; i < SL.sn; ++i) arg_plan[i] = SL.plan[SL.pos[i]];
+    std::vector<int> slot_to_arg(SL.sn);
+    for (int i = 0; i < SL.sn; ++i) slot_to_arg[SL.pos[i]] = i;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaError_t e = cudaEventCreate(&ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
-    // one untimed step first, so that the first candidate is not timed cold;
     // every batch step advances all sims together, so sims[0]->t counts them
     const int64_t t0 = sims[0]->t;
-    if (e == cudaSuccess) st = step_batch(sims, n, 1, model);
-    float best_ms = 0.0f;
-    size_t best = 0;
-    for (size_t c = 0; c < plans.size() && e == cudaSuccess && st == LBM_OK; ++c) {
-        e = cudaEventRecord(ev[0], sims[0]->stream);
-        if (e != cudaSuccess) break;
-        st = step_batch(sims, n, trial_steps, plans[c].data());
-        if (st != LBM_OK) break;
-        e = cudaEventRecord(ev[1], sims[0]->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
-            best_ms = ms;
-            best = c;
+    // one untimed step first, so that the first candidate is not timed cold
+    if (e == cudaSuccess) st = step_batch(sims, n, 1, arg_plan.data());
+    for (int g = 0; g < SL.count && e == cudaSuccess && st == LBM_OK; ++g) {
+        const int b = SL.begin[g], m = SL.begin[g + 1] - b;
+        int nch[kMaxBatch], ncol[kMaxBatch];
+        const LbmDev* devs[kMaxBatch];
+        for (int i = 0; i < m; ++i) devs[i] = &SL.sims[b + i]->dev;
+        plan_key(devs, m, nch, ncol);
+        // distinct plans of the candidate lengths, the model's first
+        std::vector<std::vector<int>> plans{std::vector<int>(SL.plan + b, SL.plan + b + m)};
+        std::vector<int> plan(m);
+        for (int L : candidate_lengths(*std::max_element(nch, nch + m))) {
+            plan_for_length(nch, m, L, plan.data());
+            if (std::find(plans.begin(), plans.end(), plan) == plans.end()) plans.push_back(plan);
         }
+        float best_ms = 0.0f;
+        size_t best = 0;
+        for (size_t c = 0; c < plans.size() && e == cudaSuccess && st == LBM_OK; ++c) {
+            for (int i = 0; i < m; ++i) arg_plan[slot_to_arg[b + i]] = plans[c][i];
+            e = cudaEventRecord(ev[0], sims[0]->stream);
+            if (e != cudaSuccess) break;
+            st = step_batch(sims, n, trial_steps, arg_plan.data());
+            if (st != LBM_OK) break;
+            e = cudaEventRecord(ev[1], sims[0]->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        for (int i = 0; i < m; ++i) arg_plan[slot_to_arg[b + i]] = plans[best][i];
+        if (e == cudaSuccess && st == LBM_OK)
+            store_plan(nch, ncol, m, SL.sims[b]->num_sms, SL.sims[b]->p.precision,
+                       plans[best].data(), true);
     }
     for (cudaEvent_t x : ev)
         if (x) cudaEventDestroy(x);
     *steps_taken = sims[0]->t - t0;
     if (st != LBM_OK) return st;
     if (e != cudaSuccess) return fail(LBM_ECUDA, "lbm_tune_batch: %s", cudaGetErrorString(e));
-    store_plan(nch, ncol, sn, sg[0]->num_sms, plans[best].data(), true);
     return LBM_OK;
 }
+
+}  // extern "C"
+
+// Enqueues the observables of the current state: the fields into s->fld, the
+// FP64 reductions into s->res, and their copy into the pinned s->h_res.
+static lbm_status observe_enqueue(lbm_sim* s)
+{
+    CUDA_TRY(fields_of(s, s->cur));
+    CUDA_TRY(launch_observe_reduce(s->dev, s->fld, s->part, kReduceBlocks, s->res, s->stream));
+    s->launches += 3;
+    CUDA_TRY(cudaMemcpyAsync(s->h_res, s->res, 13 * sizeof(double), cudaMemcpyDeviceToHost,
+                             s->stream));
+    CUDA_TRY(cudaEventRecord(s->obs_event, s->stream));
+    s->obs_t = s->t;
+    s->obs_pending = true;
+    return LBM_OK;
+}
+
+// The observables of the last enqueued evaluation, once it has completed;
+// returns the sim's status (LBM_OK, LBM_ETIMEOUT, LBM_EUNSTABLE).
+static lbm_status observe_finish(lbm_sim* s, lbm_obs* out)
+{
+    const double* r = s->h_res;
+    const double m = r[0];
+    if (out) {
+        out->t = (double)s->obs_t;
+        out->mass_phi = m;
+        out->mass_psi = r[1];
+        out->xc = m != 0 ? r[2] / m : 0.0;
+        out->yc = m != 0 ? r[3] / m : 0.0;
+        out->ux_bub = m != 0 ? r[4] / m : 0.0;
+        out->uy_bub = m != 0 ? r[5] / m : 0.0;
+        out->U_o = s->derived[4];
+        out->t_star = s->p.R > 0 ? (double)s->obs_t * s->derived[4] / s->p.R : 0.0;
+        out->nan_flag = (int32_t)r[6];
+    }
+    int timed_out = 0;
+    std::memcpy(&timed_out, r + 12, sizeof(int));
+    if (timed_out)
+        return fail(LBM_ETIMEOUT, "a kernel gave up waiting for a tile copy; results are invalid");
+    if (r[6] != 0.0 || !std::isfinite(m))
+        return fail(LBM_EUNSTABLE, "%.0f fluid nodes hold non-finite values at t = %lld", r[6],
+                    (long long)s->obs_t);
+    return LBM_OK;
+}
+
+extern "C" {
 
 lbm_status lbm_observe(lbm_sim* s, lbm_obs* out, double* host_fields)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     if (!s->ready) return fail(LBM_ESTATE, "lbm_observe before lbm_init");
     const size_t N = (size_t)s->p.nx * s->p.ny;
-    CUDA_TRY(fields_of(s, s->cur));
-    CUDA_TRY(launch_observe_reduce(s->dev, s->fld, s->part, kReduceBlocks, s->res, s->stream));
-    s->launches += 3;
-    CUDA_TRY(cudaMemcpyAsync(s->h_res, s->res, 13 * sizeof(double), cudaMemcpyDeviceToHost,
-                             s->stream));
+    lbm_status st = observe_enqueue(s);
+    if (st != LBM_OK) return st;
     if (host_fields) {
-        lbm_status st = ensure_stage(s);
+        st = ensure_stage(s);
         if (st != LBM_OK) return st;
         CUDA_TRY(cudaMemcpyAsync(s->h_stage, s->fld, 6 * N * sizeof(float),
                                  cudaMemcpyDeviceToHost, s->stream));
@@ -1021,27 +1172,34 @@ lbm_status lbm_observe(lbm_sim* s, lbm_obs* out, double* host_fields)
                     host_fields[o + x] = fluid ? (double)s->h_stage[o + x] : 0.0;
             }
     }
-    const double* r = s->h_res;
-    const double m = r[0];
-    if (out) {
-        out->t = (double)s->t;
-        out->mass_phi = m;
-        out->mass_psi = r[1];
-        out->xc = m != 0 ? r[2] / m : 0.0;
-        out->yc = m != 0 ? r[3] / m : 0.0;
-        out->ux_bub = m != 0 ? r[4] / m : 0.0;
-        out->uy_bub = m != 0 ? r[5] / m : 0.0;
-        out->U_o = s->derived[4];
-        out->t_star = s->p.R > 0 ? (double)s->t * s->derived[4] / s->p.R : 0.0;
-        out->nan_flag = (int32_t)r[6];
+    return observe_finish(s, out);
+}
+
+lbm_status lbm_observe_enqueue(lbm_sim* const* sims, int32_t n)
+{
+    lbm_status st = check_batch(sims, n, "lbm_observe_enqueue");
+    if (st != LBM_OK) return st;
+    for (int i = 0; i < n; ++i) {
+        st = observe_enqueue(sims[i]);
+        if (st != LBM_OK) return st;
     }
-    int timed_out = 0;
-    std::memcpy(&timed_out, r + 12, sizeof(int));
-    if (timed_out)
-        return fail(LBM_ETIMEOUT, "a kernel gave up waiting for a tile copy; results are invalid");
-    if (r[6] != 0.0 || !std::isfinite(m))
-        return fail(LBM_EUNSTABLE, "%.0f fluid nodes hold non-finite values at t = %lld", r[6],
-                    (long long)s->t);
+    return LBM_OK;
+}
+
+lbm_status lbm_observe_collect(lbm_sim* const* sims, int32_t n, lbm_obs* out, int32_t* status)
+{
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    if (!sims || n < 1 || n > kMaxBatch)
+        return fail(LBM_EINVAL, "lbm_observe_collect needs 1..%d sims (got %d)", kMaxBatch, n);
+    for (int i = 0; i < n; ++i) {
+        if (!sims[i]) return fail(LBM_EINVAL, "sim %d is NULL", i);
+        if (!sims[i]->obs_pending) return fail(LBM_ESTATE, "sim %d has no enqueued observation", i);
+    }
+    for (int i = 0; i < n; ++i) CUDA_TRY(cudaEventSynchronize(sims[i]->obs_event));
+    for (int i = 0; i < n; ++i) {
+        const lbm_status si = observe_finish(sims[i], &out[i]);
+        if (status) status[i] = si;
+    }
     return LBM_OK;
 }
 

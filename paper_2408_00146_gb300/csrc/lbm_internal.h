@@ -93,12 +93,15 @@ cudaError_t launch_fold_lost(const LbmDev& d, float4* mom, const float4* lost, c
 cudaError_t launch_join_planes(const LbmDev& d, int precision, const void* dev, const float4* mom,
                                int a0, int count, float* planes, cudaStream_t s);
 
-// Streaming step (FP32 storage, walls, nx a multiple of kTileX) of up to
-// kMaxBatch simulations per launch: blocks walk kTileX-wide columns in +y
+// Streaming steps of up to kMaxBatch (FP32) or kMaxBatch16 (16-bit storage)
+// simulations per launch: blocks walk columns of up to kTileX nodes in +y
 // over strips of strip_chunks[s] 8-row chunks, reading the populations
-// through tmap[s] (box {kTileX, kTileY, 36}) and tside[s] (box {4, kTileY,
-// 36}), TMA descriptors of the source buffer; first[] holds the prefix sums
-// of stream_blocks.  prepare_stream: per-device kernel attribute.
+// through TMA descriptors of the source buffer: tmap[s] (box {kTileX, 8, 36})
+// and tside[s] (side columns: box {4, 8, 36} for FP32, {8, 8, 36} for 16-bit
+// deviations), and, with 16-bit storage, tmom[s] (rest-state moments, the
+// float4 array viewed as [ny][nx][4] floats, box {4, 8, 10}); first[] holds
+// the prefix sums of stream_blocks.  prepare_stream: per-device kernel
+// attributes, before the first launch.
 struct StreamBatchArgs {
     CUtensorMap tmap[kMaxBatch];
     CUtensorMap tside[kMaxBatch];
@@ -109,13 +112,33 @@ struct StreamBatchArgs {
     int first[kMaxBatch + 1];
     int n;
 };
+constexpr int kMaxBatch16 = 48;
+struct Stream16Args {
+    CUtensorMap tmap[kMaxBatch16];
+    CUtensorMap tside[kMaxBatch16];
+    CUtensorMap tmom[kMaxBatch16];
+    LbmDev dev[kMaxBatch16];
+    void* dst[kMaxBatch16];     // deviations of the destination buffer
+    void* mdst[kMaxBatch16];    // rest-state moments of the destination buffer
+    int* err[kMaxBatch16];
+    int strip_chunks[kMaxBatch16];
+    int first[kMaxBatch16 + 1];
+    int n;
+};
+static_assert(sizeof(StreamBatchArgs) <= 32764 && sizeof(Stream16Args) <= 32764,
+              "kernel parameter limit");
 cudaError_t prepare_stream();
-bool stream_eligible(const LbmDev& d);
+// Whether a lattice of this storage precision can be stepped by the
+// streaming kernels: nx >= kTileX and a multiple of 4 (FP32) or 8 (16-bit:
+// 16-byte TMA rows), at least two chunks of fluid rows, and walls or (FP32
+// only) a periodic y axis of whole chunks.
+bool stream_eligible(const LbmDev& d, int precision);
 int stream_columns(const LbmDev& d);
-// Resident blocks per SM of the streaming kernel (its launch bounds).
-int stream_blocks_per_sm();
+// Resident blocks per SM of the streaming kernel of this precision.
+int stream_blocks_per_sm(int precision);
 int stream_blocks(const LbmDev& d, int strip_chunks);
 cudaError_t launch_stream_batch(const StreamBatchArgs& args, cudaStream_t s);
+cudaError_t launch_stream16_batch(const Stream16Args& args, int precision, cudaStream_t s);
 
 // Diagnostic: one block waits with the kernels' bounded wait (limit_ns) on a
 // barrier nothing completes and sets *flag = 1 when it gives up.

@@ -21,6 +21,7 @@
 // zeroth moments to one rounding per population instead of re-synthesising the
 // populations from a rounded sum.
 #include "lbm_internal.h"
+#include "lbm_device.cuh"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -29,101 +30,6 @@
 
 namespace {
 
-constexpr float kCs2 = 1.0f / 3.0f;
-constexpr float kW1 = 1.0f / 9.0f, kW2 = 1.0f / 36.0f;  // D2Q9 weights of axis and diagonal links
-// n = grad phi / max(|grad phi|, eps): the normal of Sec. 3 is undefined where
-// grad phi vanishes (bubble interiors, whose centre has no gradient direction);
-// the floor keeps the sharpening flux M theta n there proportional to grad phi
-// instead of following rounding noise.  It acts only where phi (1 - phi) <
-// W eps / 4 on the equilibrium profile (the far tails of the interface).
-constexpr float kNormalEps = 1e-4f;
-
-__device__ __forceinline__ int wrap(int v, int n)
-{
-    v %= n;
-    return v < 0 ? v + n : v;
-}
-
-// Source row of a stencil value at physical row y, and which wall image it is
-// (-1 bottom, +1 top, 0 none): with walls, rows at and beyond a wall mirror
-// about the wall plane (y = 1/2, y = ny - 3/2); without walls y wraps.
-__device__ __forceinline__ int src_row(const LbmDev& d, int y, int& side)
-{
-    side = 0;
-    if (!d.walls) return wrap(y, d.ny);
-    if (y < 1) {
-        side = -1;
-        y = 1 - y;
-    } else if (y > d.ny - 2) {
-        side = 1;
-        y = 2 * d.ny - 3 - y;
-    }
-    // positions farther than one reflection only feed inactive tile slots
-    return min(max(y, 1), d.ny - 2);
-}
-
-// Stencil ghost of psi at a wall mirror (side -1 below the y=0 wall, +1
-// above the y=ny-1 wall): even about the wall plane for zero-flux walls, odd
-// about psi_w when psi is held at psi_L / psi_R (psi_bc 1), as T about T_w.
-__device__ __forceinline__ float psi_ghost(const LbmDev& d, float psi, int side)
-{
-    if (d.psi_bc != 1 || side == 0) return psi;
-    return 2.0f * (side < 0 ? d.psi_L : d.psi_R) - psi;
-}
-
-// The properties rho, mu, alpha are interpolated linearly in phi (Eq. (17))
-// with phi clamped to [0, 1] (__saturatef): the conservative phase field
-// overshoots 1 by ~1e-3 inside a bubble, which at a density ratio of 1000
-// would make rho_B + (phi - 1)(rho_B - rho_A) negative.
-
-// Surface tension law, Eq. (6); ln(1 - psi) with psi clamped to [0, 1-1e-6].
-__device__ __forceinline__ float sigma_eos(const LbmDev& d, float T, float psi)
-{
-    float pc = fminf(fmaxf(psi, 0.0f), 1.0f - 1e-6f);
-    float dT = T - d.T_ref;
-    return d.sigma0 + d.s0beta_over_Tref * T * log1pf(-pc) + d.sigma_T * dT +
-           d.sigma_TT * dT * dT;
-}
-
-// Isotropic gradient 3 sum_a w_a e_a X(x + e_a) on a shared-memory array
-// (row index = y).
-template <int P>
-__device__ __forceinline__ void grad_smem(const float (*a)[P], int r, int c, float& gx, float& gy)
-{
-    const float e = a[r][c + 1], w = a[r][c - 1], n = a[r + 1][c], s = a[r - 1][c];
-    const float ne = a[r + 1][c + 1], nw = a[r + 1][c - 1], se = a[r - 1][c + 1],
-                sw = a[r - 1][c - 1];
-    gx = (1.0f / 3.0f) * (e - w) + (1.0f / 12.0f) * ((ne - nw) + (se - sw));
-    gy = (1.0f / 3.0f) * (n - s) + (1.0f / 12.0f) * ((ne - se) + (nw - sw));
-}
-
-// Inverse of the factorised central-moment transform: central moments
-// c_mn (m along x, n along y) about (ux, uy) to the nine populations.
-__device__ __forceinline__ void central_to_pop(float c00, float c10, float c01, float c20,
-                                               float c02, float c11, float c21, float c12,
-                                               float c22, float ux, float uy, float out[9])
-{
-    const float uy2 = uy * uy, ux2 = ux * ux;
-    // along y: (c_m0, c_m1, c_m2) -> partial x-moments k_m at e_y = -1, 0, +1
-    float k0m, k00, k0p, k1m, k10, k1p, k2m, k20, k2p;
-#define YPASS(a0, a1, a2, km, kz, kp)                                       \
-    kz = (a0) * (1.0f - uy2) - 2.0f * uy * (a1) - (a2);                     \
-    kp = 0.5f * ((a0) * (uy2 + uy) + (a1) * (2.0f * uy + 1.0f) + (a2));     \
-    km = 0.5f * ((a0) * (uy2 - uy) + (a1) * (2.0f * uy - 1.0f) + (a2));
-    YPASS(c00, c01, c02, k0m, k00, k0p)
-    YPASS(c10, c11, c12, k1m, k10, k1p)
-    YPASS(c20, c21, c22, k2m, k20, k2p)
-#undef YPASS
-    // along x at each e_y: (k_0, k_1, k_2) -> populations at e_x = -1, 0, +1
-#define XPASS(a0, a1, a2, fm, fz, fp)                                       \
-    fz = (a0) * (1.0f - ux2) - 2.0f * ux * (a1) - (a2);                     \
-    fp = 0.5f * ((a0) * (ux2 + ux) + (a1) * (2.0f * ux + 1.0f) + (a2));     \
-    fm = 0.5f * ((a0) * (ux2 - ux) + (a1) * (2.0f * ux - 1.0f) + (a2));
-    XPASS(k00, k10, k20, out[3], out[0], out[1])   // e_y = 0
-    XPASS(k0p, k1p, k2p, out[6], out[2], out[5])   // e_y = +1
-    XPASS(k0m, k1m, k2m, out[7], out[4], out[8])   // e_y = -1
-#undef XPASS
-}
 
 // Equilibrium-type scalar scheme (f, h, q): post-collision central moments
 // (s, a, b, s/3, s/3, 0, 0, 0, s/9).
@@ -198,88 +104,7 @@ __device__ __forceinline__ void scalar_collide(float f[9], float s, float e10, f
     add_central_increment(f, dc, ux, uy);
 }
 
-__device__ __forceinline__ float sum9(const float v[9])
-{
-    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
-}
-__device__ __forceinline__ float mx9(const float v[9])
-{
-    return (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
-}
-__device__ __forceinline__ float my9(const float v[9])
-{
-    return (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
-}
-
 enum Mode { kStep = 0, kFields = 1 };
-
-// ---- TMA / mbarrier helpers (sm_90+ PTX) -------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait: gives up once limit_ns of wall time have passed (checked
-// every 256 polls of the barrier), or after kMaxWaitPolls polls whatever the
-// timer says, instead of spinning forever.  A copy that never completes thus
-// costs its block about a second and an error flag, not a hung GPU.
-constexpr int kMaxWaitPolls = 1 << 24;
-constexpr uint64_t kWaitLimitNs = 1000000000ull;
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
-                                                  uint64_t limit_ns = kWaitLimitNs)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (int i = 1; i < kMaxWaitPolls; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255) == 0 && global_ns() - t0 > limit_ns) return false;
-    }
-    return false;
-}
-
-// One TMA copy of the box {kTileX, kTileY, 36} at (x, y, plane 0) of the
-// population tensor [36][ny][nx] into shared memory, completing on bar.
-__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                              uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(0), "r"(bar)
-        : "memory");
-}
 
 // Neighbour offsets (within one population plane) of node idx = y*nx + x,
 // x wrapping periodically and y wrapping without walls.
@@ -364,12 +189,6 @@ struct OwnPops {
     __device__ __forceinline__ float operator()(int a) const { return p[a * stride]; }
 };
 
-// The same, held in registers (a fully unrolled local array).
-struct OwnRegs {
-    const float* v;
-    __device__ __forceinline__ float operator()(int a) const { return v[a]; }
-};
-
 // Shared-memory views of one tile: its own populations [36][TY][TX] and the
 // macroscopic fields on the tile plus halo (phi with two nodes of halo, the
 // rest with one).
@@ -389,29 +208,6 @@ struct NodeMoments {
 // Moments of the own node (Eqs. (28), (34), (39), (44)) from the staged
 // populations; phi, sigma(T, psi) and p* - rho c_s^2 go to the field tiles.
 // side != 0: the slot holds a wall mirror, whose temperature is 2 T_w - T.
-// Zeroth moments of the four sets and the first moments of g at one node.
-template <class Own>
-__device__ __forceinline__ NodeMoments pop_moments(const Own& own)
-{
-    NodeMoments m;
-    float v[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = own(a);
-    m.phi = sum9(v);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = own(9 + a);
-    m.pst = sum9(v);
-    m.jx = mx9(v);
-    m.jy = my9(v);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = own(18 + a);
-    m.T = sum9(v);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = own(27 + a);
-    m.psi = sum9(v);
-    return m;
-}
-
 __device__ __forceinline__ NodeMoments own_moments(const LbmDev& d, const TileSmem& sm,
                                                    const OwnPops& own, int tx, int ty, int side)
 {
@@ -825,43 +621,20 @@ __global__ void init_equilibrium_kernel(LbmDev d, const float* __restrict__ fld,
 
 // ---- 16-bit population storage ----------------------------------------------------------
 //
-// A sim with FP16 or BF16 storage keeps, per node x and set s, the rest-state
-// moment M_s(x) of the populations x pushed at the last step (FP32, one float4
-// (f, g, h, q) per node), and per population its deviation from the
-// lattice-weighted rest state of the node that pushed it (16-bit, [36][ny][nx]):
-//     f_a(y) = w_a M(src_a(y)) + dev_a(y),   src_a(y) = y - e_a,
-// or y itself when y - e_a is a wall row (the population bounced back at y).
-// The rest part carries the conserved scalars in FP32; only the small
-// deviations (velocity, flux and non-equilibrium content) are rounded to 16
-// bits.  M is the set's zeroth moment after the collision plus the sum of the
-// nine deviations' rounding errors, so that the populations a node pushes sum
-// to its FP32 values.  All arithmetic is FP32.
-
-template <typename S> __device__ __forceinline__ float s2f(S v);
-template <> __device__ __forceinline__ float s2f<__half>(__half v) { return __half2float(v); }
-template <> __device__ __forceinline__ float s2f<__nv_bfloat16>(__nv_bfloat16 v)
-{
-    return __bfloat162float(v);
-}
-template <typename S> __device__ __forceinline__ S f2s(float v);
-template <> __device__ __forceinline__ __half f2s<__half>(float v) { return __float2half_rn(v); }
-template <> __device__ __forceinline__ __nv_bfloat16 f2s<__nv_bfloat16>(float v)
-{
-    return __float2bfloat16_rn(v);
-}
-
-__device__ __forceinline__ constexpr float w_of_dir(int a)
-{
-    return a == 0 ? 4.0f / 9.0f : (a <= 4 ? kW1 : kW2);
-}
-__device__ __forceinline__ constexpr int ex_dir(int a)
-{
-    return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
-}
-__device__ __forceinline__ constexpr int ey_dir(int a)
-{
-    return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
-}
+// A sim with FP16 or BF16 storage keeps, per node x and set s, the rest state
+// m_s(x) = M_s(x)/36 of the populations x pushed at the last step (FP32, one
+// float4 (f, g, h, q) per node; M_s the set's zeroth moment), and per
+// population its deviation from the lattice-weighted rest state of the node
+// that pushed it (16-bit, [36][ny][nx]):
+//     f_a(y) = k_a m(src_a(y)) + dev_a(y),   src_a(y) = y - e_a,
+// or y itself when y - e_a is a wall row (the population bounced back at y),
+// with the integer weights k_a = 36 w_a = 16, 4, 1: k_a m is exact in FP32 and
+// the weights sum to 36 exactly, so the conserved scalars are carried without
+// the rounding bias that the inexact FP32 weights 4/9, 1/9, 1/36 would add
+// every step.  Only the small deviations (velocity, flux and non-equilibrium
+// content) are rounded to 16 bits.  m is the post-collision zeroth moment
+// over 36 plus the nine deviations' rounding errors over 36, so that the
+// populations a node pushes sum to its FP32 values.  All arithmetic is FP32.
 
 // Rest-state moments of a tile plus three nodes of halo, [4][TY + 6][TX + 6];
 // slot (mx, my) holds the node at tile-relative (mx - 3, my - 3), wrapped in x
@@ -877,11 +650,13 @@ __device__ __forceinline__ float rebuild(const LbmDev& d, const float (*m)[kMH][
     const int ex = ex_dir(a), ey = ey_dir(a);
     const bool bounced = d.walls && (py - ey == 0 || py - ey == d.ny - 1);
     const float ms = bounced ? m[s][my][mx] : m[s][my - ey][mx - ex];
-    return fmaf(w_of_dir(a), ms, dv);
+    return fmaf(k_of_dir(a), ms, dv);
 }
 
 // Push of one set's populations (the store_set pattern) as deviations from
-// w_a M; returns the rest-state moment to record for them.
+// k_a m with m = M/36 (M: the set's post-collision zeroth moment); returns the
+// rest-state value to record for them, m plus the rounding errors of the nine
+// stored deviations over 36, so that they sum to their FP32 values.
 template <typename S, bool kEnergy>
 __device__ __forceinline__ float store_set_dev(S* __restrict__ dst_set, int N, const Nbr& nb,
                                                const float v[9], float M, int wall, float Tw)
@@ -901,10 +676,11 @@ __device__ __forceinline__ float store_set_dev(S* __restrict__ dst_set, int N, c
         out[6] = kEnergy ? -v[6] + 2.0f * kW2 * Tw : v[6];
     }
     S q[9];
+    const float m = M * kInv36;
     float lost = 0.0f;  // sum of the rounding errors of the nine deviations
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        const float dv = fmaf(-w_of_dir(a), M, out[a]);
+        const float dv = fmaf(-k_of_dir(a), m, out[a]);
         q[a] = f2s<S>(dv);
         lost += dv - s2f<S>(q[a]);
     }
@@ -934,7 +710,7 @@ __device__ __forceinline__ float store_set_dev(S* __restrict__ dst_set, int N, c
         dst_set[7 * N + o0] = q[5];
         dst_set[8 * N + o0] = q[6];
     }
-    return M + lost;
+    return fmaf(lost, kInv36, m);
 }
 
 // node_update's store for 16-bit storage: deviations pushed to the
@@ -1078,255 +854,6 @@ __global__ void __launch_bounds__(kTileX * kTileY, 4)
                             t / tiles_x);
 }
 
-// ---- streaming along y (FP32 storage, walls) -----------------------------------------
-//
-// A block owns one kTileX-wide column of the lattice over a range of 8-row
-// chunks (a strip) and walks it in +y.  Each chunk's populations, and the
-// four columns on either side of it, arrive by TMA one chunk ahead into the
-// other of two stages while the current chunk is processed.  The macroscopic
-// fields live in a 12-row window that rolls with the chunks, so the rows
-// above and below a chunk are never loaded a second time: they are rows of
-// the previous and of the current chunk.  Updating a chunk's top two rows
-// needs fields two rows further up, so those two rows are updated one
-// iteration later, from a copy of their populations (the carry).  Rows beyond
-// a wall take their fields from the mirrored fluid row, as in src_row.
-constexpr int kSideW = 4;                 // side box width: 16 bytes of FP32
-constexpr int kWin = kTileY + 4;          // rows of the field window
-
-struct StreamSmem {
-    float pop[2][36][kTileY][kTileX];           // stages: the chunk's populations
-    float side[2][2][36][kTileY][kSideW];       // stages: left and right side boxes
-    float carry[36][2][kTileX];                 // populations of the two lagging rows
-    __align__(16) float phi[kWin][kTileX + 4];  // window row j: physical row base + j
-    __align__(16) float phs[kWin][kTileX + 2];  // p* - rho c_s^2
-    __align__(16) float T[kWin][kTileX + 2];    // T (mirror rows: 2 T_w - T)
-    __align__(16) float psi[kWin][kTileX + 2];
-    __align__(16) float sig[kWin][kTileX + 2];
-    __align__(16) float nrmx[kWin - 2][kTileX + 2];   // row i: window row i + 1
-    __align__(16) float nrmy[kWin - 2][kTileX + 2];
-    uint64_t bar[2];
-};
-constexpr int kStreamSmem = (int)sizeof(StreamSmem);
-constexpr int kSideItems = 6 * kTileY;    // 8 rows x (2 outer + 2 x 2 inner) items
-constexpr uint32_t kStreamStageBytes =
-    (36u * kTileY * kTileX + 2u * 36u * kTileY * kSideW) * (uint32_t)sizeof(float);
-
-// One strip: block-local index lb is column lb % ncol, strip lb / ncol, of
-// strip_chunks chunks.
-__device__ __forceinline__ void stream_strip(const LbmDev& d, float* __restrict__ dst,
-                                             const CUtensorMap* tmap, const CUtensorMap* tside,
-                                             int strip_chunks, int* __restrict__ err, int lb)
-{
-    extern __shared__ __align__(128) unsigned char s_raw[];
-    StreamSmem& S = *reinterpret_cast<StreamSmem*>(s_raw);
-    constexpr int NT = kTileX * kTileY;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * kTileX + tx;
-    const int ncol = d.nx / kTileX;
-    const int x0 = (lb % ncol) * kTileX;
-    const int nchunks = (d.nfy + kTileY - 1) / kTileY;
-    const int c0 = (lb / ncol) * strip_chunks;
-    const int c1 = min(c0 + strip_chunks, nchunks);
-    if (c0 >= c1) return;
-    const int xl = x0 == 0 ? d.nx - kSideW : x0 - kSideW;
-    const int xr = x0 + kTileX == d.nx ? 0 : x0 + kTileX;
-    // chunk c0 - 1 is read only for its fields and its top two rows (whose
-    // update this strip owns); the last strip ends with an iteration that
-    // has no chunk and updates the final carry
-    const int kfirst = c0 > 0 ? c0 - 1 : 0;
-    const int klast = c1 == nchunks ? c1 : c1 - 1;
-    const TileSmem sm{nullptr, S.phi, &S.sig[1], &S.phs[1], S.nrmx, S.nrmy};
-
-    if (tid == 0) {
-        mbar_init(smem_addr(&S.bar[0]), 1);
-        mbar_init(smem_addr(&S.bar[1]), 1);
-    }
-    __syncthreads();
-    auto issue = [&](int k) {   // chunk k into stage k & 1 (one thread)
-        const int st = k & 1;
-        const uint32_t bar = smem_addr(&S.bar[st]);
-        const int y = d.y0 + k * kTileY;
-        mbar_expect_tx(bar, kStreamStageBytes);
-        tma_load_tile(smem_addr(&S.pop[st][0][0][0]), tmap, x0, y, bar);
-        tma_load_tile(smem_addr(&S.side[st][0][0][0][0]), tside, xl, y, bar);
-        tma_load_tile(smem_addr(&S.side[st][1][0][0][0]), tside, xr, y, bar);
-    };
-    if (tid == 0) {
-        issue(kfirst);
-        if (kfirst + 1 < c1) issue(kfirst + 1);
-    }
-    uint32_t parity = 0;        // bit st: wait parity of stage st
-
-    // node of the chunk whose moments this thread computes: row (ty + 6) % 8,
-    // so that for ty >= 2 it is the node the thread updates in the same
-    // iteration (chunk row ty - 2)
-    const int rb = (ty + kTileY - 2) % kTileY;
-    for (int k = kfirst; k <= klast; ++k) {
-        const bool have = k < c1;
-        const int st = k & 1;
-        const int base = d.y0 + k * kTileY - 4;     // physical row of window row 0
-        const bool walled = base < 1 || base + kWin - 1 > d.ny - 2;
-        NodeMoments m{};
-        float pv[36];
-        if (have) {
-            const bool ok = mbar_wait_bounded(smem_addr(&S.bar[st]), (parity >> st) & 1u);
-            parity ^= 1u << st;
-            if (__syncthreads_or(!ok)) {
-                // a copy did not arrive in time: report it, and keep the block
-                // resident for one more bounded wait on each stage so that no
-                // transfer into its shared memory outlives it
-                if (tid == 0) {
-                    atomicExch(err, 1);
-                    mbar_wait_bounded(smem_addr(&S.bar[st]), ((parity >> st) & 1u) ^ 1u);
-                    if (k + 1 < c1)
-                        mbar_wait_bounded(smem_addr(&S.bar[st ^ 1]), (parity >> (st ^ 1)) & 1u);
-                }
-                return;
-            }
-            // fields of the chunk's rows (window rows 4..11)
-#pragma unroll
-            for (int a = 0; a < 36; ++a) pv[a] = S.pop[st][a][rb][tx];
-            m = pop_moments(OwnRegs{pv});
-            S.phi[4 + rb][tx + 2] = m.phi;
-            S.phs[4 + rb][tx + 1] = m.pst - (d.rhoA + __saturatef(m.phi) * d.drho) * kCs2;
-            S.T[4 + rb][tx + 1] = m.T;
-            S.psi[4 + rb][tx + 1] = m.psi;
-            S.sig[4 + rb][tx + 1] = sigma_eos(d, m.T, m.psi);
-            if (tid >= NT - kSideItems) {
-                // side nodes x0-2, x0+33 (phi) and x0-1, x0+32 (phi and
-                // p* - rho c_s^2; T, psi and sigma): one item per thread
-                const int it = tid - (NT - kSideItems);
-                const int r = it % kTileY, item = it / kTileY;     // item 0..5
-                const bool outer = item < 2;
-                const int lr = outer ? item : (item - 2) / 2;      // 0 left, 1 right
-                const int f = outer ? 0 : (item - 2) % 2;          // 0: sets f, g; 1: h, q
-                const int bc = outer ? (lr ? 1 : 2) : (lr ? 0 : 3);
-                const float* sp = &S.side[st][lr][f * 18][r][bc];
-                constexpr int P = kTileY * kSideW;                 // plane stride
-                float v[9];
-#pragma unroll
-                for (int a = 0; a < 9; ++a) v[a] = sp[a * P];
-                const float s1 = sum9(v);
-                const int c = lr ? kTileX + 1 : 0;                 // column in the 34-wide arrays
-                if (outer) {
-                    S.phi[4 + r][lr ? kTileX + 3 : 0] = s1;
-                } else {
-#pragma unroll
-                    for (int a = 0; a < 9; ++a) v[a] = sp[(9 + a) * P];
-                    const float s2 = sum9(v);
-                    if (f == 0) {
-                        S.phi[4 + r][c + 1] = s1;
-                        S.phs[4 + r][c] = s2 - (d.rhoA + __saturatef(s1) * d.drho) * kCs2;
-                    } else {
-                        S.T[4 + r][c] = s1;
-                        S.psi[4 + r][c] = s2;
-                        S.sig[4 + r][c] = sigma_eos(d, s1, s2);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // rows of the window beyond a wall: the mirrored fluid row's fields
-        if (walled) {
-            for (int i = tid; i < kWin * (kTileX + 4); i += NT) {
-                const int j = i / (kTileX + 4), c = i % (kTileX + 4);
-                const int y = base + j;
-                if (y >= 1 && y <= d.ny - 2) continue;
-                const int js = (y < 1 ? 1 - y : 2 * d.ny - 3 - y) - base;
-                if (js < 0 || js >= kWin) continue;
-                S.phi[j][c] = S.phi[js][c];
-                if (c >= 1 && c <= kTileX + 2) {
-                    S.phs[j][c - 1] = S.phs[js][c - 1];
-                    const float pm = psi_ghost(d, S.psi[js][c - 1], y < 1 ? -1 : 1);
-                    S.psi[j][c - 1] = pm;
-                    const float Tm = 2.0f * (y < 1 ? d.T_H : d.T_C) - S.T[js][c - 1];
-                    S.T[j][c - 1] = Tm;
-                    S.sig[j][c - 1] = sigma_eos(d, Tm, pm);
-                }
-            }
-            __syncthreads();
-        }
-        if (k >= c0) {
-            // normals on window rows 1..10; rows 1 and 2 were rows 9 and 10
-            // of the previous iteration (rolled), unless this is the strip's
-            // first update or the window reaches a wall
-            const int j0 = (k == c0 || walled) ? 1 : 3;
-            for (int i = tid + (j0 - 1) * (kTileX + 2); i < (kWin - 2) * (kTileX + 2); i += NT) {
-                const int jr = i / (kTileX + 2), c = i % (kTileX + 2);
-                float gxp, gyp;
-                grad_smem<kTileX + 4>(S.phi, jr + 1, c + 1, gxp, gyp);
-                const float inv = fminf(rsqrtf(gxp * gxp + gyp * gyp), 1.0f / kNormalEps);
-                S.nrmx[jr][c] = gxp * inv;
-                S.nrmy[jr][c] = gyp * inv;
-            }
-            __syncthreads();
-            // update window row ty + 2: the carry (ty < 2) or chunk row ty - 2
-            const int gy = base + ty + 2;
-            if (gy >= 1 && gy <= d.ny - 2 && (ty < 2 || have)) {
-                if (ty < 2) {
-#pragma unroll
-                    for (int a = 0; a < 36; ++a) pv[a] = S.carry[a][ty][tx];
-                    m = pop_moments(OwnRegs{pv});
-                }
-                node_update<kStep>(d, sm, m, OwnRegs{pv}, StoreF32{dst}, dst, tx, ty, x0 + tx, gy);
-            }
-        }
-        __syncthreads();
-        if (have) {
-            // the chunk's top two rows become the carry (16-byte copies)
-            for (int i = tid; i < 36 * 2 * kTileX / 4; i += NT) {
-                const int a = i / (2 * kTileX / 4), q = i % (2 * kTileX / 4);
-                reinterpret_cast<float4*>(&S.carry[a][0][0])[q] =
-                    reinterpret_cast<const float4*>(&S.pop[st][a][kTileY - 2][0])[q];
-            }
-        }
-        // the window rolls by 8 rows: rows 8..11 -> 0..3 (fields), 9..10 ->
-        // 1..2 (normals)
-        {
-            constexpr int W4 = kTileX + 4, W2 = kTileX + 2;
-            constexpr int n4 = 4 * W4 / 4, n2 = 4 * W2 / 4, m2 = 2 * W2 / 4;
-            static_assert((4 * W4) % 4 == 0 && (4 * W2) % 4 == 0 && (2 * W2) % 4 == 0,
-                          "whole float4 rows");
-            for (int i = tid; i < n4 + 4 * n2 + 2 * m2; i += NT) {
-                if (i < n4) {
-                    reinterpret_cast<float4*>(&S.phi[0][0])[i] =
-                        reinterpret_cast<const float4*>(&S.phi[kTileY][0])[i];
-                    continue;
-                }
-                int q = i - n4;
-                if (q < 4 * n2) {
-                    const int w = q / n2;
-                    float(*arr)[W2] = w == 0 ? S.phs : (w == 1 ? S.T : (w == 2 ? S.psi : S.sig));
-                    q %= n2;
-                    reinterpret_cast<float4*>(&arr[0][0])[q] =
-                        reinterpret_cast<const float4*>(&arr[kTileY][0])[q];
-                    continue;
-                }
-                q -= 4 * n2;
-                float(*arr)[W2] = q < m2 ? S.nrmx : S.nrmy;
-                q %= m2;
-                reinterpret_cast<float4*>(&arr[0][0])[q] =
-                    reinterpret_cast<const float4*>(&arr[kTileY][0])[q];
-            }
-        }
-        __syncthreads();
-        if (tid == 0 && k + 2 < c1) issue(k + 2);
-    }
-}
-
-// Streaming step of up to kMaxBatch simulations in one launch: block b runs
-// strip b - first[s] of simulation s (first[s] <= b < first[s + 1]).  A
-// single simulation's step is a batch of one, so a simulation steps through
-// the same code whether it is batched or not.
-__global__ void __launch_bounds__(kTileX * kTileY, 2)
-    stream_batch_kernel(const __grid_constant__ StreamBatchArgs args)
-{
-    int s = 0;
-    while (s + 1 < args.n && (int)blockIdx.x >= args.first[s + 1]) ++s;
-    stream_strip(args.dev[s], static_cast<float*>(args.dst[s]), &args.tmap[s], &args.tside[s],
-                 args.strip_chunks[s], args.err[s], blockIdx.x - args.first[s]);
-}
-
 // Source node of population a at fluid node (x, y) for the rest-state
 // reference: y - e_a, or (x, y) itself when y - e_a is a wall row.
 __device__ __forceinline__ int src_node(const LbmDev& d, int x, int y, int a)
@@ -1360,7 +887,7 @@ __global__ void split_planes_kernel(LbmDev d, const float* __restrict__ pl, int 
     for (int k = 0; k < count; ++k) {
         const int a = (a0 + k) % 9, s = (a0 + k) / 9;
         float4 mv = mom[src_node(d, x, y, a)];
-        const float dv = pl[(size_t)k * N + o] - w_of_dir(a) * comp(mv, s);
+        const float dv = fmaf(-k_of_dir(a), comp(mv, s), pl[(size_t)k * N + o]);
         const S q = f2s<S>(dv);
         dev[(size_t)(a0 + k) * N + o] = q;
         comp(l, s) += dv - s2f<S>(q);
@@ -1368,9 +895,9 @@ __global__ void split_planes_kernel(LbmDev d, const float* __restrict__ pl, int 
     lost[o] = l;
 }
 
-// mom += lost at every fluid node: the populations held at a node then sum,
-// over the lattice, to the FP32 values they were split from (each node's M is
-// referenced once per direction, with weights summing to 1).
+// mom += lost / 36 at every fluid node: the populations held at a node then
+// sum, over the lattice, to the FP32 values they were split from (each node's
+// m is referenced once per direction, with integer weights summing to 36).
 __global__ void fold_lost_kernel(LbmDev d, float4* __restrict__ mom,
                                  const float4* __restrict__ lost)
 {
@@ -1379,7 +906,8 @@ __global__ void fold_lost_kernel(LbmDev d, float4* __restrict__ mom,
     if (x >= d.nx || fy >= d.nfy) return;
     const int o = (d.y0 + fy) * d.nx + x;
     const float4 m = mom[o], l = lost[o];
-    mom[o] = make_float4(m.x + l.x, m.y + l.y, m.z + l.z, m.w + l.w);
+    mom[o] = make_float4(fmaf(l.x, kInv36, m.x), fmaf(l.y, kInv36, m.y), fmaf(l.z, kInv36, m.z),
+                         fmaf(l.w, kInv36, m.w));
 }
 
 // FP32 populations a0 .. a0 + count - 1 rebuilt from 16-bit storage into
@@ -1401,14 +929,14 @@ __global__ void join_planes_kernel(LbmDev d, const S* __restrict__ dev,
         if (fluid) {
             const float4 mv = mom[src_node(d, x, y, a)];
             const float ms = s == 0 ? mv.x : (s == 1 ? mv.y : (s == 2 ? mv.z : mv.w));
-            v = w_of_dir(a) * ms + s2f<S>(dev[(size_t)(a0 + k) * N + o]);
+            v = fmaf(k_of_dir(a), ms, s2f<S>(dev[(size_t)(a0 + k) * N + o]));
         }
         pl[(size_t)k * N + o] = v;
     }
 }
 
 // Initial state of a sim with 16-bit storage: the equilibria of
-// equilibrium_set as deviations from w_a M(src_a), where M = (phi, p, T, psi)
+// equilibrium_set as deviations from k_a m(src_a), where 36 m = (phi, p, T, psi)
 // of the fields (the zeroth moments of the four equilibria).
 template <typename S>
 __global__ void init_dev_kernel(LbmDev d, const float* __restrict__ fld, S* __restrict__ dev,
@@ -1428,15 +956,17 @@ __global__ void init_dev_kernel(LbmDev d, const float* __restrict__ fld, S* __re
         lost[s] = 0.0f;
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            const float ms = fld[(size_t)kField[s] * N + src_node(d, x, y, a)];
-            const float dv = out[a] - w_of_dir(a) * ms;
+            const float ms = fld[(size_t)kField[s] * N + src_node(d, x, y, a)] * kInv36;
+            const float dv = fmaf(-k_of_dir(a), ms, out[a]);
             const S q = f2s<S>(dv);
             dev[(size_t)(9 * s + a) * N + o] = q;
             lost[s] += dv - s2f<S>(q);
         }
     }
-    mom[o] = make_float4(fld[o] + lost[0], fld[3 * N + o] + lost[1], fld[4 * N + o] + lost[2],
-                         fld[5 * N + o] + lost[3]);
+    mom[o] = make_float4(fmaf(lost[0], kInv36, fld[o] * kInv36),
+                         fmaf(lost[1], kInv36, fld[3 * N + o] * kInv36),
+                         fmaf(lost[2], kInv36, fld[4 * N + o] * kInv36),
+                         fmaf(lost[3], kInv36, fld[5 * N + o] * kInv36));
 }
 
 // Analytic initial fields: tanh bubble (Sec. 3 profile), fluid at rest, T
@@ -1718,34 +1248,6 @@ cudaError_t launch_join_planes(const LbmDev& d, int precision, const void* dev, 
             d, static_cast<const __nv_bfloat16*>(dev), mom, a0, count, planes);
     else
         return cudaErrorInvalidValue;
-    return cudaGetLastError();
-}
-
-cudaError_t prepare_stream()
-{
-    return cudaFuncSetAttribute(stream_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kStreamSmem);
-}
-
-bool stream_eligible(const LbmDev& d)
-{
-    return d.walls && d.nx % kTileX == 0 && d.nfy >= 2 * kTileY;
-}
-
-int stream_columns(const LbmDev& d) { return d.nx / kTileX; }
-
-int stream_blocks_per_sm() { return 2; }
-
-int stream_blocks(const LbmDev& d, int strip_chunks)
-{
-    const int ncol = d.nx / kTileX;
-    const int nchunks = (d.nfy + kTileY - 1) / kTileY;
-    return ncol * ((nchunks + strip_chunks - 1) / strip_chunks);
-}
-
-cudaError_t launch_stream_batch(const StreamBatchArgs& args, cudaStream_t s)
-{
-    stream_batch_kernel<<<args.first[args.n], dim3(kTileX, kTileY), kStreamSmem, s>>>(args);
     return cudaGetLastError();
 }
 

@@ -58,7 +58,8 @@ STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA"
 EXPORTS = [
     "lbm_derive", "lbm_workspace_bytes", "lbm_create", "lbm_create_ex", "lbm_init", "lbm_step",
     "lbm_step_batch", "lbm_batch_plan", "lbm_tune_batch",
-    "lbm_observe", "lbm_get_populations", "lbm_get_derived", "lbm_launch_count",
+    "lbm_observe", "lbm_observe_enqueue", "lbm_observe_collect",
+    "lbm_get_populations", "lbm_get_derived", "lbm_launch_count",
     "lbm_destroy", "lbm_last_error", "lbm_reduce_observables_noalloc", "lbm_probe_bounded_wait",
 ]
 
@@ -106,6 +107,10 @@ def load() -> ctypes.CDLL:
             L.lbm_tune_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_int64)]
             L.lbm_observe.argtypes = [vp, ctypes.POINTER(LbmObs), dp]
+            L.lbm_observe_enqueue.argtypes = [ctypes.POINTER(vp), ctypes.c_int32]
+            L.lbm_observe_collect.argtypes = [ctypes.POINTER(vp), ctypes.c_int32,
+                                              ctypes.POINTER(LbmObs),
+                                              ctypes.POINTER(ctypes.c_int32)]
             L.lbm_get_populations.argtypes = [vp, fp]
             L.lbm_get_derived.argtypes = [vp, dp]
             L.lbm_launch_count.argtypes = [vp]
@@ -234,6 +239,28 @@ def lbm_observe(sim, host_fields: np.ndarray | None = None, check: bool = True) 
     out = {n: getattr(ob, n) for n in OBS_FIELDS}
     out["nan_flag"] = ob.nan_flag
     out["status"] = st
+    return out
+
+
+def lbm_observe_enqueue(sims):
+    """Enqueues the observables of every sim (one stream) without waiting."""
+    arr, n = _handles(sims)
+    _check(load().lbm_observe_enqueue(arr, n), "lbm_observe_enqueue")
+
+
+def lbm_observe_collect(sims) -> list[dict]:
+    """Waits for the observables lbm_observe_enqueue enqueued and returns one
+    dict per sim (with its 'status')."""
+    arr, n = _handles(sims)
+    obs = (LbmObs * n)()
+    st = (ctypes.c_int32 * n)()
+    _check(load().lbm_observe_collect(arr, n, obs, st), "lbm_observe_collect")
+    out = []
+    for i in range(n):
+        d = {k: getattr(obs[i], k) for k in OBS_FIELDS}
+        d["nan_flag"] = obs[i].nan_flag
+        d["status"] = int(st[i])
+        out.append(d)
     return out
 
 

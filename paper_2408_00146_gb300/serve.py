@@ -3,15 +3,22 @@
 Requests (one parameter set each, arriving over time) are admitted while
 their device workspaces fit a memory budget, kept resident, and advanced
 together: every round steps all resident simulations by ``round_steps``
-time steps with ``lbm_step_batch`` (one kernel launch per step and storage
-precision for up to 64 simulations), then reads each one's observables.  A
-simulation finishes when its bubble velocity |U| (the phi-weighted mean
-velocity of Sec. 6) falls below ``tol`` after having exceeded 100 tol (the
-bubble starts at rest) or it reaches its step cap; its
-memory is released and waiting requests are admitted before the next round
-(continuous batching).  Each simulation's trajectory is independent of what
-else is resident, because a batched step computes every simulation exactly
-as a step of its own would.
+time steps with ``lbm_step_batch`` (one launch per step and kernel family for
+up to 64 simulations).  Rounds are pipelined: the observables of every
+resident simulation after a round are enqueued on the device
+(``lbm_observe_enqueue``) and read (``lbm_observe_collect``) while the next
+round runs, so the host's bookkeeping never leaves the GPU idle.
+
+A simulation reaches its terminal state when its bubble velocity |U| (the
+phi-weighted mean velocity of Sec. 6) has stayed below ``tol`` at every
+observation over a window of at least one characteristic time t* = R/U_o
+(Eq. (21)) and two rounds; a bubble that sloshes through U = 0 exceeds tol
+within such a window and does not stop.  A simulation also stops at its step
+cap.  Its memory is then released and waiting requests are admitted before
+the next round (continuous batching).  Each simulation's trajectory is
+independent of what else is resident, because a batched step computes every
+simulation exactly as a step of its own would, and the decisions depend only
+on its own observations.
 
 The scheduler only orders work on the host; every step of every simulation
 runs in the CUDA kernels behind the C ABI.  ``Server`` takes an engine
@@ -34,6 +41,7 @@ class Request:
     arrival: float = 0.0           # seconds after the start of the run
     max_steps: int = 300_000
     tol: float = 1e-6
+    window_steps: int | None = None    # terminal window; None: max(t*, 2 rounds)
 
 
 @dataclasses.dataclass
@@ -77,8 +85,15 @@ class LbmEngine:
         for i in range(0, len(sims), MAX_BATCH):
             self.lbm.lbm_step_batch(sims[i:i + MAX_BATCH], n)
 
-    def observe(self, sim) -> dict:
-        return sim.observe(check=False)
+    def observe_enqueue(self, sims: list) -> None:
+        for i in range(0, len(sims), MAX_BATCH):
+            self.lbm.lbm_observe_enqueue(sims[i:i + MAX_BATCH])
+
+    def observe_collect(self, sims: list) -> list[dict]:
+        out = []
+        for i in range(0, len(sims), MAX_BATCH):
+            out += self.lbm.lbm_observe_collect(sims[i:i + MAX_BATCH])
+        return out
 
     def close(self, sim) -> None:
         sim.close()
@@ -109,15 +124,27 @@ class Server:
         self.peak_bytes = 0
         self.peak_resident = 0
 
+    def window(self, req: Request, ob: dict) -> int:
+        """Steps over which |U| must stay below tol: the request's own, else
+        t* = R/U_o (from the observation) and at least two rounds."""
+        if req.window_steps is not None:
+            return int(req.window_steps)
+        w = 2 * self.round_steps
+        uo, R = ob.get("U_o", 0.0), float(req.params.get("R", 0.0))
+        if uo > 0 and R > 0:
+            w = max(w, int(math.ceil(R / uo)))
+        return w
+
     def run(self, requests: list[Request]) -> list[Result]:
         for r in requests:
             if self.engine.workspace_bytes(r.params) > self.budget:
                 raise ValueError(f"request {r.rid} needs more memory than the whole budget")
         pending = deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         waiting: list[Request] = []
-        resident: dict[int, dict] = {}        # rid -> {req, sim, bytes, steps, admitted}
+        resident: dict[int, dict] = {}        # rid -> {req, sim, bytes, steps, admitted, ...}
         used = 0
         results: list[Result] = []
+        inflight: list[tuple[int, int]] = []  # (rid, steps) of the enqueued observation
         t0 = self.clock()
 
         def now() -> float:
@@ -134,7 +161,7 @@ class Server:
                 if used + nbytes <= self.budget:
                     used += nbytes
                     resident[r.rid] = dict(req=r, sim=self.engine.open(r.params), bytes=nbytes,
-                                           steps=0, admitted=now(), moving=False)
+                                           steps=0, admitted=now(), last_fast=0)
                 else:
                     still.append(r)
             waiting = still
@@ -149,29 +176,39 @@ class Server:
             self.engine.step([resident[k]["sim"] for k in order], self.round_steps)
             self.rounds += 1
             for k in order:
+                resident[k]["steps"] += self.round_steps
+                self.node_steps += fluid_nodes(resident[k]["req"].params) * self.round_steps
+            # the previous round's observables, read while this round runs
+            live = [(k, st) for k, st in inflight if k in resident]
+            obs = self.engine.observe_collect([resident[k]["sim"] for k, _ in live]) if live else []
+            for (k, st), ob in zip(live, obs):
                 ent = resident[k]
-                ent["steps"] += self.round_steps
-                self.node_steps += fluid_nodes(ent["req"].params) * self.round_steps
-                ob = self.engine.observe(ent["sim"])
+                req = ent["req"]
                 u = math.hypot(ob["ux_bub"], ob["uy_bub"])
                 status = None
-                ent["moving"] = ent["moving"] or u >= 100.0 * ent["req"].tol
                 if ob.get("status", 0) != 0 or not math.isfinite(u):
                     status = f"error {ob.get('status', 0)}"
-                elif ent["moving"] and u < ent["req"].tol:
-                    status = "converged"
-                elif ent["steps"] >= ent["req"].max_steps:
-                    status = "step cap"
+                else:
+                    if u >= req.tol:
+                        ent["last_fast"] = st
+                    if st - ent["last_fast"] >= self.window(req, ob):
+                        status = "converged"
+                    elif st >= req.max_steps:
+                        status = "step cap"
                 if status is None:
                     continue
                 self.engine.close(ent["sim"])
                 used -= ent["bytes"]
-                r = ent["req"]
-                results.append(Result(rid=r.rid, arrival=r.arrival, admitted=ent["admitted"],
-                                      finished=now(), steps=ent["steps"],
-                                      converged=status == "converged", status=status,
-                                      obs=dict(ob), nodes=fluid_nodes(r.params)))
+                results.append(Result(rid=req.rid, arrival=req.arrival, admitted=ent["admitted"],
+                                      finished=now(), steps=st, converged=status == "converged",
+                                      status=status, obs=dict(ob),
+                                      nodes=fluid_nodes(req.params)))
                 del resident[k]
+            # observables after this round, collected during the next one
+            order = sorted(resident)
+            if order:
+                self.engine.observe_enqueue([resident[k]["sim"] for k in order])
+            inflight = [(k, resident[k]["steps"]) for k in order]
         return sorted(results, key=lambda r: r.rid)
 
 
@@ -188,10 +225,17 @@ def percentile(values: list[float], q: float) -> float:
 
 
 def summary(results: list[Result], wall_s: float, node_steps: int) -> dict:
+    """Latency percentiles over all requests, and separately over those that
+    reached their terminal state and those stopped by the step cap."""
     lat = [r.latency for r in results]
+    conv = [r.latency for r in results if r.converged]
+    cap = [r.latency for r in results if r.status == "step cap"]
     return {"requests": len(results),
-            "converged": sum(r.converged for r in results),
+            "converged": len(conv), "capped": len(cap),
+            "errors": len(results) - len(conv) - len(cap),
             "p50_latency_s": percentile(lat, 50.0), "p99_latency_s": percentile(lat, 99.0),
+            "p50_converged_s": percentile(conv, 50.0), "p99_converged_s": percentile(conv, 99.0),
+            "p50_capped_s": percentile(cap, 50.0), "p99_capped_s": percentile(cap, 99.0),
             "mlups": node_steps / wall_s / 1e6 if wall_s > 0 else float("nan"),
             "wall_s": wall_s}
 

@@ -20,11 +20,16 @@ def lbm():
 
 
 def _mix():
-    """Three streaming lattices (walls, nx a multiple of 32) of different
-    heights, one FP32 tile-kernel lattice (nx = 48) and one binary16 one."""
-    ps = [si.scaled_channel(64, 160), si.scaled_channel(96, 66), si.scaled_channel(32, 290),
-          si.scaled_channel(48, 64), si.scaled_channel(64, 96)]
+    """Three FP32 streaming lattices of different heights (80 x 66 with a
+    partial last column of 16 nodes; 32 x 290), one FP32 tile-kernel lattice
+    (nx = 45: no 16-byte TMA rows), one binary16 tile-kernel lattice (nx = 60)
+    and binary16 and bfloat16 streaming lattices (launches of their own)."""
+    ps = [si.scaled_channel(64, 160), si.scaled_channel(80, 66), si.scaled_channel(32, 290),
+          si.scaled_channel(45, 64), si.scaled_channel(60, 96), si.scaled_channel(48, 80),
+          si.scaled_channel(40, 72)]
     ps[4]["precision"] = 1
+    ps[5]["precision"] = 1
+    ps[6]["precision"] = 2
     for p in ps:
         p["R"] = min(p["R"], 8.0)
     return ps
@@ -44,6 +49,7 @@ def test_plan_reports_streaming_and_tile_sims(lbm):
     plan = lbm.lbm_batch_plan(sims)
     assert len(plan) == len(ps)
     assert all(c >= 4 for c in plan[:3]) and plan[3] == 0 and plan[4] == 0
+    assert plan[5] >= 4 and plan[6] >= 4
     assert lbm.lbm_batch_plan(sims) == plan          # cached: the same answer again
 
 
@@ -61,7 +67,8 @@ def test_tuned_batch_equals_untuned_batch(lbm):
         assert np.array_equal(a.populations(), b.populations())
     # the tuned plan is what later batch steps use, and it keeps the result
     plan = lbm.lbm_batch_plan(tuned)
-    assert all(c >= 4 for c in plan[:3]) and plan[3:] == [0, 0]
+    assert all(c >= 4 for c in plan[:3]) and plan[3:5] == [0, 0]
+    assert plan[5] >= 4 and plan[6] >= 4
     lbm.lbm_step_batch(tuned, 5)
     lbm.lbm_step_batch(plain, 5)
     for a, b in zip(tuned, plain):
@@ -71,7 +78,7 @@ def test_tuned_batch_equals_untuned_batch(lbm):
 def test_tune_without_streaming_sims_and_bad_arguments(lbm):
     import torch
     st = torch.cuda.Stream()
-    tile_only = _sims(lbm, [si.scaled_channel(48, 64)], st)
+    tile_only = _sims(lbm, [si.scaled_channel(45, 64)], st)
     assert lbm.lbm_tune_batch(tile_only, 3) == 0
     assert tile_only[0].observe()["t"] == 0
     sims = _sims(lbm, _mix()[:2], st)

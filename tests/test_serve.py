@@ -22,9 +22,9 @@ class FakeClock:
 
 
 class FakeEngine:
-    """Simulations whose bubble velocity halves every step from U0 = 1e-3,
-    so a request with tolerance tol converges after ceil(log2(1e-3 / tol))
-    steps; each round costs one unit of virtual time per resident sim."""
+    """Simulations whose bubble velocity halves every step from U0 = 1e-3;
+    each round costs one unit of virtual time.  Observations are enqueued
+    (the state is recorded) and collected later, as on the device."""
 
     def __init__(self, clock):
         self.clock = clock
@@ -38,7 +38,7 @@ class FakeEngine:
     def open(self, p):
         self.open_now += 1
         self.max_open = max(self.max_open, self.open_now)
-        return {"p": p, "t": 0}
+        return {"p": p, "t": 0, "seen": None}
 
     def step(self, sims, n):
         self.log.append(len(sims))
@@ -46,9 +46,16 @@ class FakeEngine:
         for s in sims:
             s["t"] += n
 
-    def observe(self, s):
-        u = 1e-3 * 0.5 ** s["t"]
-        return {"ux_bub": 0.0, "uy_bub": u, "status": 0, "yc": float(s["t"])}
+    def velocity(self, t):
+        return 1e-3 * 0.5 ** t
+
+    def observe_enqueue(self, sims):
+        for s in sims:
+            s["seen"] = s["t"]
+
+    def observe_collect(self, sims):
+        return [{"ux_bub": 0.0, "uy_bub": self.velocity(s["seen"]), "status": 0,
+                 "yc": float(s["seen"])} for s in sims]
 
     def close(self, s):
         self.open_now -= 1
@@ -58,9 +65,16 @@ class StartupEngine(FakeEngine):
     """The bubble starts at rest: |U| = 0 until step 10, then 1e-3 halving
     every step."""
 
-    def observe(self, s):
-        u = 0.0 if s["t"] < 10 else 1e-3 * 0.5 ** (s["t"] - 10)
-        return {"ux_bub": u, "uy_bub": 0.0, "status": 0}
+    def velocity(self, t):
+        return 0.0 if t < 10 else 1e-3 * 0.5 ** (t - 10)
+
+
+class SloshEngine(FakeEngine):
+    """A bubble oscillating about its equilibrium: U = 1e-3 cos(2 pi t / 40),
+    which is sampled exactly at a zero crossing every 20 steps."""
+
+    def velocity(self, t):
+        return abs(1e-3 * math.cos(2.0 * math.pi * t / 40.0))
 
 
 def _req(rid, nx, arrival=0.0, tol=1e-9, max_steps=1000):
@@ -78,15 +92,16 @@ def test_budget_and_continuous_batching():
     res = srv.run(reqs)
     assert [r.rid for r in res] == list(range(5))
     assert eng.max_open == 2 and srv.peak_bytes <= budget
-    # 1e-3 * 2^-t < 1e-9 first at t = 20: four rounds of 5 steps
-    assert all(r.steps == 20 and r.converged for r in res)
-    # admitted in arrival order as slots free: 0,1 at t=0; 2,3 after 4
-    # rounds; 4 after 8 rounds
+    # 1e-3 * 2^-t < 1e-9 first at t = 20; |U| < tol over a window of two
+    # rounds (10 steps) after the last fast observation (t = 15) holds at
+    # t = 25, which is read one round later (pipelined rounds)
+    assert all(r.steps == 25 and r.converged for r in res)
+    # admitted in arrival order as slots free: 0,1 at t=0; 2,3 after 6
+    # rounds; 4 after 12 rounds
     adm = [r.admitted for r in res]
-    assert adm[0] == adm[1] == 0.0
-    assert adm[2] == adm[3] == 4.0 and adm[4] == 8.0
-    assert eng.log == [2] * 8 + [1] * 4
-    assert srv.node_steps == 5 * 20 * 64 * 254
+    assert adm == [0.0, 0.0, 6.0, 6.0, 12.0]
+    assert eng.log == [2] * 12 + [1] * 6
+    assert srv.node_steps == 5 * 30 * 64 * 254
 
 
 def test_first_fit_admission_and_arrivals():
@@ -115,18 +130,41 @@ def test_step_cap_and_oversized_request():
         Server(eng, 100, clock=clk, wait=clk.wait).run([_req(1, 64)])
 
 
-def test_bubble_at_rest_at_start_is_not_converged():
+def test_rest_shorter_than_the_window_is_not_terminal():
     clk = FakeClock()
     srv = Server(StartupEngine(clk), 10 ** 9, round_steps=5, clock=clk, wait=clk.wait)
     (r,) = srv.run([_req(0, 64, tol=1e-9)])
-    # moving at t = 10 (1e-3 >= 100 tol); below 1e-9 first at t = 30
-    assert r.converged and r.steps == 30
+    # at rest for 5 steps (< the 10-step window); moving from t = 10, fast
+    # until t = 25, below tol at t = 30 and 35
+    assert r.converged and r.steps == 35
+
+
+def test_sloshing_bubble_does_not_pass_the_terminal_test():
+    """|U| sampled at a zero crossing (every 20 steps) is below tol, but the
+    samples between are not: only the step cap stops it."""
+    clk = FakeClock()
+    srv = Server(SloshEngine(clk), 10 ** 9, round_steps=10, clock=clk, wait=clk.wait)
+    (r,) = srv.run([_req(0, 64, tol=1e-6, max_steps=400)])
+    assert r.status == "step cap" and r.steps == 400
+
+
+def test_window_is_one_characteristic_time():
+    """Without a request window the terminal window is t* = R/U_o from the
+    observation (Eq. (21)), and at least two rounds."""
+    srv = Server(FakeEngine(FakeClock()), 10 ** 9, round_steps=100)
+    req = _req(0, 64)
+    assert srv.window(req, {"U_o": req.params["R"] / 5000.0}) == 5000
+    assert srv.window(req, {"U_o": 1.0}) == 200
+    assert srv.window(req, {}) == 200
+    req.window_steps = 30
+    assert srv.window(req, {"U_o": 1e-3}) == 30
 
 
 def test_error_status_finishes_request():
     clk = FakeClock()
     eng = FakeEngine(clk)
-    eng.observe = lambda s: {"ux_bub": math.nan, "uy_bub": 0.0, "status": -4}
+    eng.observe_collect = lambda sims: [{"ux_bub": math.nan, "uy_bub": 0.0, "status": -4}
+                                        for _ in sims]
     srv = Server(eng, 10 ** 9, clock=clk, wait=clk.wait)
     (r,) = srv.run([_req(0, 64)])
     assert r.status.startswith("error") and not r.converged
@@ -139,6 +177,7 @@ def test_percentile_matches_linear_interpolation():
         assert percentile(v, q) == pytest.approx(float(np.percentile(v, q)))
     s = summary([], 1.0, 0)
     assert s["requests"] == 0 and math.isnan(s["p50_latency_s"])
+    assert s["converged"] == s["capped"] == s["errors"] == 0
 
 
 def test_request_stream_shapes():
@@ -165,6 +204,7 @@ def test_result_alone_equals_result_in_the_mix():
     stream = si.request_stream(n=6, rate=1e9, seed=5, nx_range=(64, 160))
     reqs = [Request(rid=i, params=p, arrival=0.0, max_steps=300, tol=1e-12)
             for i, (_, p) in enumerate(stream)]
+    # the observation reaching the 300-step cap is read one round later
     eng = LbmEngine()
     ws = [lbm.lbm_workspace_bytes(r.params) for r in reqs]
     mix = Server(eng, budget_bytes=sum(sorted(ws)[-3:]), round_steps=100).run(reqs)
