@@ -110,8 +110,58 @@ def profiled_traffic(work: str, mode: str, precision: str, params=None):
     return float(ent["dram_bytes_per_launch"])
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (the driver's libnvidia-ml):
+    current and maximum SM clock and the active clock-event reasons."""
+
+    CLOCK_SM = 1
+    # clock-event reason bits of the NVML API
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown",
+               0x20: "sw_thermal_slowdown", 0x4: "sw_power_cap"}
+
+    def __init__(self, device_index: int):
+        import ctypes
+        self.c = ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.lib = lib
+        self.h = ctypes.c_void_p()
+        uuid = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+        except Exception:
+            uuid = None
+        rc = 1
+        if uuid:
+            rc = lib.nvmlDeviceGetHandleByUUID(("GPU-" + uuid).encode(), ctypes.byref(self.h))
+        if rc != 0:
+            rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device_index),
+                                                   ctypes.byref(self.h))
+        if rc != 0:
+            lib.nvmlShutdown()
+            raise OSError("no NVML handle for the device")
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+
+    def sample(self) -> tuple[float, float, list[str]]:
+        c = self.c
+        sm, mx, rs = c.c_uint(), c.c_uint(), c.c_ulonglong()
+        self.lib.nvmlDeviceGetClockInfo(self.h, self.CLOCK_SM, c.byref(sm))
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.CLOCK_SM, c.byref(mx))
+        self.reasons_fn(self.h, c.byref(rs))
+        return float(sm.value), float(mx.value), [n for b, n in self.REASONS.items()
+                                                  if rs.value & b]
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
 class ClockSampler:
-    """nvidia-smi clock/throttle samples during the timed region."""
+    """SM clock and throttle samples during the timed region: NVML polled
+    from a host thread every 0.5 ms (a region of a few milliseconds still
+    gets samples), else nvidia-smi every 200 ms."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -120,9 +170,33 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.tmp = None
+        self.rows: list[tuple[float, float, list[str]]] = []   # inside the region
+        self.edges: list[tuple[float, float, list[str]]] = []  # just before and after
+        self.source = "nvml"
+        self.thread = None
+        self.stop = False
+        try:
+            self.nvml = _Nvml(device_index)
+        except (OSError, AttributeError):
+            self.nvml = None
+            self.source = "nvidia-smi"
+
+    def _poll(self):
+        while not self.stop:
+            self.rows.append(self.nvml.sample())
+            time.sleep(0.0005)
 
     def __enter__(self):
+        if self.nvml is not None:
+            import threading
+            self.edges.append(self.nvml.sample())
+            self.switch = sys.getswitchinterval()
+            sys.setswitchinterval(0.0002)
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return self
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
@@ -133,6 +207,12 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
+        if self.thread is not None:
+            self.stop = True
+            self.thread.join()
+            sys.setswitchinterval(self.switch)
+            self.edges.append(self.nvml.sample())
+            self.nvml.close()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -140,24 +220,32 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self) -> dict:
-        self.tmp.flush()
+    def _smi_rows(self):
         rows = []
+        if self.tmp is None:
+            return rows
+        self.tmp.flush()
         with open(self.tmp.name) as fh:
             for line in fh:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                             "sw_power_cap"]
+                    rows.append((float(parts[1]),
+                                 float(parts[2]) if parts[2].replace(".", "").isdigit() else 0.0,
+                                 [names[i] for i in range(4) if parts[5 + i] == "Active"]))
         os.unlink(self.tmp.name)
+        return rows
+
+    def summary(self) -> dict:
+        rows = (self.rows or self.edges) if self.nvml is not None else self._smi_rows()
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    "source": self.source}
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted({n for r in rows for n in r[2]}),
+                "samples": len(rows), "source": self.source}
 
 
 def max_over_ranks(ms: float, device: str) -> float:
@@ -351,7 +439,7 @@ def sub_measure(lbm, torch, dev_index, params, precision, mode, steps, tune_step
            "achieved_gbs": gbs, "hbm_frac": gbs / peak,
            "bytes_per_node_step": BYTES_PER_NODE_STEP[precision],
            "strip_chunks": sorted(set(lbm.lbm_batch_plan(b.sims)) - {0}),
-           "clocks": {"sm_mhz": c["sm_mhz"], "reasons": c["reasons"]}}
+           "clocks": {"sm_mhz": c["sm_mhz"], "reasons": c["reasons"], "samples": c["samples"]}}
     b.close()
     return out
 
@@ -429,7 +517,7 @@ def run_gpu(args) -> None:
             "batched_fp16_ensemble": ens, "plain_fp32_single": plain,
             "ratio": ens["value"] / plain["value"],
             "target_ratio": 2.0,
-            "note": "64 channels of uneven size (nx 128..512, multiples of 32; ny = 4 nx) at "
+            "note": "64 channels of uneven size (nx 128..512, multiples of 16; ny = 4 nx) at "
                     "binary16 storage in one lbm_step_batch call, against lbm_step on one "
                     "256x1024 FP32 channel"}
         extra["config3"] = {
@@ -438,7 +526,9 @@ def run_gpu(args) -> None:
             for prec in ("fp32", "fp16", "bf16")}
 
     e2e = run_e2e(args, lbm, torch, stream, params) if not args.no_e2e else None
-    served = run_served(args, torch) if (args.serve_requests > 0 and rank == 0) else None
+    plain_value = extra.get("mixed_precision", {}).get("plain_fp32_single", {}).get("value")
+    served = (run_served(args, torch, plain_value) if (args.serve_requests > 0 and rank == 0)
+              else None)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -469,7 +559,8 @@ def run_gpu(args) -> None:
             "served": served,
             "gpu_launches": launches,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
-                       "reasons": clocks["reasons"]},
+                       "reasons": clocks["reasons"], "samples": clocks["samples"],
+                       "source": clocks["source"]},
         }
         line.update(extra)
         print(json.dumps(line), flush=True)
@@ -477,17 +568,22 @@ def run_gpu(args) -> None:
         dist.destroy_process_group()
 
 
-def run_served(args, torch) -> dict:
+def run_served(args, torch, plain_value=None) -> dict:
     """The served workload: a Poisson stream of requests (uneven lattices,
     physics and storage precisions) through the serving loop, arrivals in
-    wall time; p50/p99 of arrival-to-finish latency and aggregate MLUPS."""
+    wall time.  A request ends at its terminal state (|U| < 1e-6 at every
+    observation over a window of t* = R/U_o) or at the step cap.  Reports the
+    converged and capped counts, p50/p99 of arrival-to-finish latency over all
+    requests and over each class, and aggregate MLUPS (also against the plain
+    single-simulation rate when given)."""
     from paper_2408_00146_gb300.serve import LbmEngine, Server, requests_from_stream, summary
 
-    stream = si.request_stream(n=args.serve_requests, rate=args.serve_rate, seed=0)
+    stream = si.request_stream(n=args.serve_requests, rate=args.serve_rate, seed=0,
+                               start=args.serve_start, nx_range=(64, args.serve_nx_max))
     reqs = requests_from_stream(stream, max_steps=args.serve_max_steps, tol=1e-6)
     free, _total = torch.cuda.mem_get_info()
     budget = int(min(150e9, 0.8 * free))
-    srv = Server(LbmEngine(), budget_bytes=budget, round_steps=100)
+    srv = Server(LbmEngine(), budget_bytes=budget, round_steps=args.serve_round_steps)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res = srv.run(reqs)
@@ -495,10 +591,13 @@ def run_served(args, torch) -> dict:
     wall = time.perf_counter() - t0
     out = summary(res, wall, srv.node_steps)
     out.update({"rate_per_s": args.serve_rate, "max_steps": args.serve_max_steps,
-                "tol": 1e-6, "round_steps": 100, "budget_gb": budget / 1e9,
+                "tol": 1e-6, "terminal_window": "t* = R/U_o (at least two rounds)",
+                "round_steps": args.serve_round_steps, "budget_gb": budget / 1e9,
                 "peak_resident": srv.peak_resident, "peak_gb": srv.peak_bytes / 1e9,
                 "fp16_requests": sum(p["precision"] == 1 for _, p in stream),
-                "lattices": "nx log-uniform 64..512 (x16), ny = 4 nx"})
+                "lattices": f"nx log-uniform 64..{args.serve_nx_max} (x16), ny = 4 nx",
+                "start": args.serve_start,
+                "vs_plain": out["mlups"] / plain_value if plain_value else None})
     return out
 
 
@@ -573,10 +672,18 @@ def main():
                     help="skip the mixed_precision and config3 sub-results")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=48,
+    ap.add_argument("--serve-requests", type=int, default=500,
                     help="requests of the served workload (0: skip it)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--serve-max-steps", type=int, default=3000)
+    ap.add_argument("--serve-max-steps", type=int, default=4000,
+                    help="step cap of a served request (its terminal state is usually "
+                         "10^5-10^6 steps away; see the served block's converged count)")
+    ap.add_argument("--serve-round-steps", type=int, default=128)
+    ap.add_argument("--serve-nx-max", type=int, default=512)
+    ap.add_argument("--serve-start", default="quarter", choices=["quarter", "reference_plane"],
+                    help="quarter: the bubble a quarter of the way along the channel (the "
+                         "configured stream); reference_plane: a clean bubble on the "
+                         "reference-temperature plane, which reaches its terminal state")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

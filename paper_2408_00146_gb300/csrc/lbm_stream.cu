@@ -34,7 +34,10 @@
 namespace {
 
 constexpr int NT = kTileX * kTileY;       // threads per block, one node each
-constexpr int kSideItems = 6 * kTileY;    // side-node work items per chunk
+// Side nodes of a chunk: phi at the outer columns -2 and w + 1, all four
+// zeroth moments at the inner columns -1 and w: six items per row, (phi),
+// (phi, p*) or (T, psi), taken by the last 48 threads of the block.
+constexpr int kSideItems = 6 * kTileY;
 
 // one-dimensional rest populations E_i(0): 1/6, 2/3, 1/6 at e = -1, 0, +1
 __device__ __forceinline__ constexpr float e0_of(int i) { return i == 1 ? 2.0f / 3.0f : 1.0f / 6.0f; }
@@ -203,37 +206,44 @@ __device__ __forceinline__ void put_fields(const LbmDev& d, Window<SLOTS>& W, in
     if (phys == d.ny - 3) W.phi[(r + 3) & M][c + 2] = phi;
 }
 
-// The same for a side item that carries only some of the fields: phi (and,
-// with p*, the pressure field), or T and psi (sigma).
+// phi of a side node (column c, window row r, physical row phys) and its
+// wall mirrors, as put_fields.
 template <int SLOTS>
-__device__ __forceinline__ void put_side(const LbmDev& d, Window<SLOTS>& W, int r, int phys, int c,
-                                         int what, float a0, float a1)
+__device__ __forceinline__ void put_side_phi(const LbmDev& d, Window<SLOTS>& W, int r, int phys,
+                                             int c, float phi)
 {
     constexpr int M = SLOTS - 1;
+    if (d.walls && phys > d.ny - 2) return;
+    W.phi[r & M][c + 2] = phi;
+    if (!d.walls) return;
+    if (phys == 1) W.phi[(r - 1) & M][c + 2] = phi;
+    if (phys == d.ny - 2) W.phi[(r + 1) & M][c + 2] = phi;
+    if (phys == 2) W.phi[(r - 3) & M][c + 2] = phi;
+    if (phys == d.ny - 3) W.phi[(r + 3) & M][c + 2] = phi;
+}
+
+// phi and p* - rho c_s^2 (what = 1; a0 = phi, a1 = p*) or sigma (what = 2;
+// a0 = T, a1 = psi) of an inner side node and their wall mirrors, as
+// put_fields.
+template <int SLOTS>
+__device__ __forceinline__ void put_side_pair(const LbmDev& d, Window<SLOTS>& W, int r, int phys,
+                                              int c, int what, float a0, float a1)
+{
+    constexpr int M = SLOTS - 1;
+    if (what == 1) put_side_phi(d, W, r, phys, c, a0);
     if (d.walls && phys > d.ny - 2) return;
     const bool mir = d.walls && (phys == 1 || phys == d.ny - 2);
     const int side = phys == 1 ? -1 : 1;
     const int rm = r + side;
-    if (what == 0) {            // phi only (outer columns)
-        W.phi[r & M][c + 2] = a0;
-        if (mir) W.phi[rm & M][c + 2] = a0;
-    } else if (what == 1) {     // phi and p* - rho c_s^2 (a0 = phi, a1 = p*)
+    if (what == 1) {
         const float phs = a1 - (d.rhoA + __saturatef(a0) * d.drho) * kCs2;
-        W.phi[r & M][c + 2] = a0;
         W.phs[r & M][c + 1] = phs;
-        if (mir) {
-            W.phi[rm & M][c + 2] = a0;
-            W.phs[rm & M][c + 1] = phs;
-        }
-    } else {                    // sigma from T = a0, psi = a1
+        if (mir) W.phs[rm & M][c + 1] = phs;
+    } else {
         W.sig[r & M][c + 1] = sigma_eos(d, a0, a1);
         if (mir)
             W.sig[rm & M][c + 1] =
                 sigma_eos(d, 2.0f * (side < 0 ? d.T_H : d.T_C) - a0, psi_ghost(d, a1, side));
-    }
-    if (what <= 1 && d.walls) {
-        if (phys == 2) W.phi[(r - 3) & M][c + 2] = a0;
-        if (phys == d.ny - 3) W.phi[(r + 3) & M][c + 2] = a0;
     }
 }
 
@@ -607,7 +617,9 @@ struct Smem16 {
 //   issue(k, st): copies of chunk k into stage st (one thread);
 //   bytes: transaction bytes of one stage;
 //   own_moments(st, rb, tx, phys): the 14 moments of chunk row rb, column tx;
-//   side_item(st, it, r, phys, Y): one of the kSideItems side-node items of row r.
+//   side_item(st, item, r, phys, rw, W): side item 0 .. 5 of chunk row r (items
+//     0, 1: phi at columns -2, w + 1; 2..5: (phi, p*) or (T, psi) at columns -1
+//     and w).
 template <int S, int SLOTS, class Stage, class Out>
 __device__ __forceinline__ void walk(const LbmDev& d, const Strip& sp, Stage& stg, Window<SLOTS>& W,
                                      uint64_t* bars, int* __restrict__ err, const Out& out)
@@ -723,24 +735,24 @@ struct Stage32 {
         const bool outer = item < 2;
         const int lr = outer ? item : (item - 2) / 2;
         const int f = outer ? 0 : (item - 2) % 2;
-        const int bc = outer ? (lr ? 1 : 2) : (lr ? 0 : 3);
+        const int c = outer ? (lr ? sp.w + 1 : -2) : (lr ? sp.w : -1);
+        const int bc = lr ? c - sp.w : c + 4;
         const float* p = &sm.side[st][lr][f * 18][r][bc];
         constexpr int P = kTileY * 4;
         float v[9], t[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) v[a] = p[a * P];
-        float rr = diffs32(v, t);
-        const float s1 = fmaf(36.0f, rr, sum_t(t));
-        const int c = outer ? (lr ? sp.w + 1 : -2) : (lr ? sp.w : -1);
+        float r0 = diffs32(v, t);
+        const float s1 = fmaf(36.0f, r0, sum_t(t));
         if (outer) {
-            put_side(d, W, rw, phys, c, 0, s1, 0.0f);
+            put_side_phi(d, W, rw, phys, c, s1);
             return;
         }
 #pragma unroll
         for (int a = 0; a < 9; ++a) v[a] = p[(9 + a) * P];
-        rr = diffs32(v, t);
-        const float s2 = fmaf(36.0f, rr, sum_t(t));
-        put_side(d, W, rw, phys, c, f == 0 ? 1 : 2, s1, s2);
+        r0 = diffs32(v, t);
+        const float s2 = fmaf(36.0f, r0, sum_t(t));
+        put_side_pair(d, W, rw, phys, c, f == 0 ? 1 : 2, s1, s2);
     }
 };
 
@@ -786,42 +798,63 @@ struct Stage16 {
     {
         return sm.mom[st][(c + 8) >> 3][rr + 1][(c + 8) & 7];
     }
-    // The differences t_a = f_a - k_a r of one set of a node, r its own rest
+    // The differences t_a = f_a - k_a r of a node's populations, r its own rest
     // value: f_a = k_a m(src_a) + dev_a with src_a the node the population came
     // from (itself where it bounced off a wall), so t_a = k_a (m(src_a) - r) +
-    // dev_a, exact up to the rounding of that small sum.
-    template <class Dev>
-    __device__ __forceinline__ float diffs16(int st, int c, int rr, int phys, int set,
-                                             const Dev& dev, float t[9]) const
+    // dev_a, exact up to the rounding of that small sum.  Direction by
+    // direction: one float4 load (four sets) per source node, and the sums
+    // accumulated in the order a = 0..8 (sum_seq), which every evaluation of a
+    // node's fields shares.
+    template <int NSET, int SET0, class Dev, class Acc>
+    __device__ __forceinline__ void diffs16(int st, int c, int rr, int phys, const Dev& dev,
+                                            float4 m0, const Acc& acc) const
     {
         const bool bot = d.walls && phys == 1, top = d.walls && phys == d.ny - 2;
-        const float4 m0 = mom_at(st, c, rr);
-        const float r = set == 0 ? m0.x : (set == 1 ? m0.y : (set == 2 ? m0.z : m0.w));
+        const float r[4] = {m0.x, m0.y, m0.z, m0.w};
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
             const int ex = ex_dir(a), ey = ey_dir(a);
             const bool own = a == 0 || (ey > 0 && bot) || (ey < 0 && top);
-            float ms = r;
-            if (!own) {
-                const float4 m4 = mom_at(st, c - ex, rr - ey);
-                ms = set == 0 ? m4.x : (set == 1 ? m4.y : (set == 2 ? m4.z : m4.w));
+            const float4 m4 = own ? m0 : mom_at(st, c - ex, rr - ey);
+            const float ms[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+            for (int k = 0; k < NSET; ++k) {
+                const int set = SET0 + k;
+                acc(k, a, fmaf(k_of_dir(a), ms[set] - r[set], s2f<T16>(dev(9 * set + a))));
             }
-            t[a] = fmaf(k_of_dir(a), ms - r, s2f<T16>(dev(9 * set + a)));
         }
-        return r;
     }
     template <class Dev>
     __device__ __forceinline__ Mom rebuild_moments(int st, int c, int rr, int phys,
                                                    const Dev& dev) const
     {
+        const float4 m0 = mom_at(st, c, rr);
+        SetMom sm4[4];
+        float gnd = 0.0f, gxy = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sm4[k] = SetMom{0.0f, 0.0f, 0.0f, 0.0f};
+        diffs16<4, 0>(st, c, rr, phys, dev, m0, [&](int k, int a, float t) {
+            const int ex = ex_dir(a), ey = ey_dir(a);
+            sm4[k].d += t;
+            if (ex) sm4[k].jx += ex * t;
+            if (ey) sm4[k].jy += ey * t;
+            if (k == 1) {
+                if (ex != 0 && ey == 0) gnd += t;
+                if (ex == 0 && ey != 0) gnd -= t;
+                if (ex != 0 && ey != 0) gxy += (ex * ey) * t;
+            }
+        });
+        sm4[0].r = m0.x;
+        sm4[1].r = m0.y;
+        sm4[2].r = m0.z;
+        sm4[3].r = m0.w;
         Mom m;
-        float t[9];
-        m.f = set_moments(diffs16(st, c, rr, phys, 0, dev, t), t);
-        m.g = set_moments(diffs16(st, c, rr, phys, 1, dev, t), t);
-        m.gnd = (t[1] + t[3]) - (t[2] + t[4]);
-        m.gxy = (t[5] + t[7]) - (t[6] + t[8]);
-        m.h = set_moments(diffs16(st, c, rr, phys, 2, dev, t), t);
-        m.q = set_moments(diffs16(st, c, rr, phys, 3, dev, t), t);
+        m.f = sm4[0];
+        m.g = sm4[1];
+        m.h = sm4[2];
+        m.q = sm4[3];
+        m.gnd = gnd;
+        m.gxy = gxy;
         return m;
     }
     __device__ __forceinline__ Mom own_moments(int st, int rb, int tx, int phys) const
@@ -841,17 +874,25 @@ struct Stage16 {
         const T16* p = &sm.side[st][lr][0][r][bc];
         constexpr int P = kTileY * 8;
         const auto dev = [&](int i) { return p[i * P]; };
-        const int set1 = f == 0 ? 0 : 2;
-        float t[9];
-        float rr = diffs16(st, c, r, phys, set1, dev, t);
-        const float s1 = fmaf(36.0f, rr, sum_t(t));
+        const float4 m0 = mom_at(st, c, r);
         if (outer) {
-            put_side(d, W, rw, phys, c, 0, s1, 0.0f);
+            float dd = 0.0f;
+            diffs16<1, 0>(st, c, r, phys, dev, m0, [&](int, int, float t) { dd += t; });
+            put_side_phi(d, W, rw, phys, c, fmaf(36.0f, m0.x, dd));
             return;
         }
-        rr = diffs16(st, c, r, phys, set1 + 1, dev, t);
-        const float s2 = fmaf(36.0f, rr, sum_t(t));
-        put_side(d, W, rw, phys, c, f == 0 ? 1 : 2, s1, s2);
+        float d1 = 0.0f, d2 = 0.0f;
+        const auto acc2 = [&](int k, int, float t) {
+            if (k == 0) d1 += t;
+            else d2 += t;
+        };
+        if (f == 0) {
+            diffs16<2, 0>(st, c, r, phys, dev, m0, acc2);
+            put_side_pair(d, W, rw, phys, c, 1, fmaf(36.0f, m0.x, d1), fmaf(36.0f, m0.y, d2));
+        } else {
+            diffs16<2, 2>(st, c, r, phys, dev, m0, acc2);
+            put_side_pair(d, W, rw, phys, c, 2, fmaf(36.0f, m0.z, d1), fmaf(36.0f, m0.w, d2));
+        }
     }
 };
 

@@ -55,6 +55,7 @@ class Result:
     status: str                    # "converged", "step cap" or an error
     obs: dict
     nodes: int
+    storage: int = 0               # population storage: 0 FP32, 1 binary16, 2 bfloat16
 
     @property
     def latency(self) -> float:
@@ -202,7 +203,8 @@ class Server:
                 results.append(Result(rid=req.rid, arrival=req.arrival, admitted=ent["admitted"],
                                       finished=now(), steps=st, converged=status == "converged",
                                       status=status, obs=dict(ob),
-                                      nodes=fluid_nodes(req.params)))
+                                      nodes=fluid_nodes(req.params),
+                                      storage=int(req.params.get("precision", 0))))
                 del resident[k]
             # observables after this round, collected during the next one
             order = sorted(resident)
@@ -224,18 +226,36 @@ def percentile(values: list[float], q: float) -> float:
     return v[lo] + (v[hi] - v[lo]) * (pos - lo)
 
 
-def summary(results: list[Result], wall_s: float, node_steps: int) -> dict:
-    """Latency percentiles over all requests, and separately over those that
-    reached their terminal state and those stopped by the step cap."""
-    lat = [r.latency for r in results]
+STORAGE_NAMES = {0: "fp32", 1: "fp16", 2: "bf16"}
+
+
+def _classes(results: list[Result]) -> dict:
     conv = [r.latency for r in results if r.converged]
     cap = [r.latency for r in results if r.status == "step cap"]
-    return {"requests": len(results),
-            "converged": len(conv), "capped": len(cap),
+    steps = [r.steps for r in results if r.converged]
+    return {"requests": len(results), "converged": len(conv), "capped": len(cap),
             "errors": len(results) - len(conv) - len(cap),
-            "p50_latency_s": percentile(lat, 50.0), "p99_latency_s": percentile(lat, 99.0),
             "p50_converged_s": percentile(conv, 50.0), "p99_converged_s": percentile(conv, 99.0),
             "p50_capped_s": percentile(cap, 50.0), "p99_capped_s": percentile(cap, 99.0),
+            "p50_steps_to_terminal": percentile(steps, 50.0)}
+
+
+def summary(results: list[Result], wall_s: float, node_steps: int) -> dict:
+    """Latency percentiles over all requests, and separately over those that
+    reached their terminal state and those stopped by the step cap; the same
+    split per population storage format."""
+    lat = [r.latency for r in results]
+    out = _classes(results)
+    out.pop("requests")
+    by = {}
+    for code, name in STORAGE_NAMES.items():
+        sub = [r for r in results if r.storage == code]
+        if sub:
+            by[name] = _classes(sub)
+    return {"requests": len(results), **{k: out[k] for k in ("converged", "capped", "errors")},
+            "p50_latency_s": percentile(lat, 50.0), "p99_latency_s": percentile(lat, 99.0),
+            **{k: v for k, v in out.items() if k not in ("converged", "capped", "errors")},
+            "by_storage": by,
             "mlups": node_steps / wall_s / 1e6 if wall_s > 0 else float("nan"),
             "wall_s": wall_s}
 

@@ -163,14 +163,15 @@ def parity_fields(p: dict, seed: int = 0) -> np.ndarray:
 
 # ---- ensembles and request streams ------------------------------------------------
 
-def ensemble_channels(n: int = 64, seed: int = 0, nx_range=(128, 512)) -> list[dict]:
+def ensemble_channels(n: int = 64, seed: int = 0, nx_range=(128, 512), nx_step: int = 16
+                      ) -> list[dict]:
     """n independent channels of uneven size and physics: nx uniform over the
-    multiples of 32 in nx_range, ny = 4 nx, bubble R = nx/8 a quarter of the
-    way along the channel; Gibbs elasticity beta ~ U(0, 0.3), quadratic
+    multiples of nx_step in nx_range, ny = 4 nx, bubble R = nx/8 a quarter of
+    the way along the channel; Gibbs elasticity beta ~ U(0, 0.3), quadratic
     sensitivity sigma_TT log-uniform in [2e-4, 4e-3], Marangoni number
     Ma ~ U(5, 50); the rest as the 64x128 channel."""
     rng = np.random.default_rng(seed)
-    sizes = np.arange(nx_range[0], nx_range[1] + 1, 32)
+    sizes = np.arange(nx_range[0], nx_range[1] + 1, nx_step)
     out = []
     for _ in range(n):
         nx = int(rng.choice(sizes))
@@ -184,12 +185,17 @@ def ensemble_channels(n: int = 64, seed: int = 0, nx_range=(128, 512)) -> list[d
 
 
 def request_stream(n: int = 500, rate: float = 20.0, seed: int = 0, nx_range=(64, 512),
-                   fp16_share: float = 0.5) -> list[tuple[float, dict]]:
+                   fp16_share: float = 0.5, start: str = "quarter") -> list[tuple[float, dict]]:
     """Poisson request arrivals (exponential gaps of mean 1/rate seconds) of
     channels with nx log-uniform in nx_range rounded to a multiple of 16,
     ny = 4 nx, the physics distributions of ensemble_channels, and 16-bit
-    population storage with probability fp16_share.  Returns (arrival
-    time in seconds, parameters) pairs in arrival order."""
+    population storage with probability fp16_share.  start = "quarter": the
+    bubble a quarter of the way along the channel; "reference_plane": a clean
+    bubble (beta = 0) on the reference-temperature plane y = ny/2, the
+    equilibrium of the self-rewetting law (Sec. 6).  Returns (arrival time in
+    seconds, parameters) pairs in arrival order."""
+    if start not in ("quarter", "reference_plane"):
+        raise ValueError(start)
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -203,5 +209,7 @@ def request_stream(n: int = 500, rate: float = 20.0, seed: int = 0, nx_range=(64
                  sigma_TT=float(np.exp(rng.uniform(np.log(2e-4), np.log(4e-3)))),
                  Ma=float(rng.uniform(5.0, 50.0)),
                  precision=1 if rng.uniform() < fp16_share else 0)
+        if start == "reference_plane":
+            p.update(yb=2.0 * nx, beta=0.0)
         out.append((t, p))
     return out

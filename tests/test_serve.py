@@ -180,6 +180,22 @@ def test_percentile_matches_linear_interpolation():
     assert s["converged"] == s["capped"] == s["errors"] == 0
 
 
+def test_summary_splits_by_storage():
+    from paper_2408_00146_gb300.serve import Result
+    mk = lambda rid, lat, conv, st: Result(rid=rid, arrival=0.0, admitted=0.0, finished=lat,
+                                           steps=100 * rid, converged=conv,
+                                           status="converged" if conv else "step cap",
+                                           obs={}, nodes=1, storage=st)
+    res = [mk(1, 1.0, True, 0), mk(2, 3.0, True, 0), mk(3, 9.0, False, 1), mk(4, 2.0, True, 1)]
+    s = summary(res, 1.0, 0)
+    assert (s["converged"], s["capped"], s["errors"]) == (3, 1, 0)
+    assert s["p50_converged_s"] == 2.0 and s["p50_capped_s"] == 9.0
+    assert s["by_storage"]["fp32"]["converged"] == 2 and s["by_storage"]["fp32"]["capped"] == 0
+    assert s["by_storage"]["fp16"]["capped"] == 1
+    assert s["by_storage"]["fp16"]["p50_steps_to_terminal"] == 400
+    assert "bf16" not in s["by_storage"]
+
+
 def test_request_stream_shapes():
     st = si.request_stream(n=200, rate=20.0, seed=3)
     t = np.array([a for a, _ in st])
