@@ -160,7 +160,7 @@ class _Nvml:
 
 class ClockSampler:
     """SM clock and throttle samples during the timed region: NVML polled
-    from a host thread every 0.5 ms (a region of a few milliseconds still
+    from a host thread every 0.2 ms (a region of a few milliseconds still
     gets samples), else nvidia-smi every 200 ms."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -185,7 +185,7 @@ class ClockSampler:
     def _poll(self):
         while not self.stop:
             self.rows.append(self.nvml.sample())
-            time.sleep(0.0005)
+            time.sleep(0.0002)
 
     def __enter__(self):
         if self.nvml is not None:
@@ -527,8 +527,15 @@ def run_gpu(args) -> None:
 
     e2e = run_e2e(args, lbm, torch, stream, params) if not args.no_e2e else None
     plain_value = extra.get("mixed_precision", {}).get("plain_fp32_single", {}).get("value")
-    served = (run_served(args, torch, plain_value) if (args.serve_requests > 0 and rank == 0)
-              else None)
+    served = None
+    if args.serve_requests > 0 and ws == 1:
+        # requests that reach their terminal state, then the config's own
+        # lattice range and start at a step cap (throughput of the mix)
+        served = run_served(args, torch, "reference_plane", args.serve_nx_max,
+                            args.serve_max_steps, plain_value)
+        if args.serve_throughput_steps > 0:
+            extra["served_throughput"] = run_served(args, torch, "quarter", 512,
+                                                    args.serve_throughput_steps, plain_value)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -568,19 +575,20 @@ def run_gpu(args) -> None:
         dist.destroy_process_group()
 
 
-def run_served(args, torch, plain_value=None) -> dict:
+def run_served(args, torch, start: str, nx_max: int, max_steps: int,
+               plain_value=None) -> dict:
     """The served workload: a Poisson stream of requests (uneven lattices,
     physics and storage precisions) through the serving loop, arrivals in
     wall time.  A request ends at its terminal state (|U| < 1e-6 at every
     observation over a window of t* = R/U_o) or at the step cap.  Reports the
     converged and capped counts, p50/p99 of arrival-to-finish latency over all
-    requests and over each class, and aggregate MLUPS (also against the plain
-    single-simulation rate when given)."""
+    requests and over each class (also per storage format), and aggregate
+    MLUPS (also against the plain single-simulation rate when given)."""
     from paper_2408_00146_gb300.serve import LbmEngine, Server, requests_from_stream, summary
 
     stream = si.request_stream(n=args.serve_requests, rate=args.serve_rate, seed=0,
-                               start=args.serve_start, nx_range=(64, args.serve_nx_max))
-    reqs = requests_from_stream(stream, max_steps=args.serve_max_steps, tol=1e-6)
+                               start=start, nx_range=(64, nx_max))
+    reqs = requests_from_stream(stream, max_steps=max_steps, tol=1e-6)
     free, _total = torch.cuda.mem_get_info()
     budget = int(min(150e9, 0.8 * free))
     srv = Server(LbmEngine(), budget_bytes=budget, round_steps=args.serve_round_steps)
@@ -590,15 +598,24 @@ def run_served(args, torch, plain_value=None) -> dict:
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     out = summary(res, wall, srv.node_steps)
-    out.update({"rate_per_s": args.serve_rate, "max_steps": args.serve_max_steps,
+    out.update({"rate_per_s": args.serve_rate, "max_steps": max_steps,
                 "tol": 1e-6, "terminal_window": "t* = R/U_o (at least two rounds)",
                 "round_steps": args.serve_round_steps, "budget_gb": budget / 1e9,
                 "peak_resident": srv.peak_resident, "peak_gb": srv.peak_bytes / 1e9,
                 "fp16_requests": sum(p["precision"] == 1 for _, p in stream),
-                "lattices": f"nx log-uniform 64..{args.serve_nx_max} (x16), ny = 4 nx",
-                "start": args.serve_start,
+                "lattices": f"nx log-uniform 64..{nx_max} (x16), ny = 4 nx",
+                "start": START_NOTE[start],
                 "vs_plain": out["mlups"] / plain_value if plain_value else None})
     return out
+
+
+START_NOTE = {
+    "quarter": "bubble a quarter of the way along the channel (config physics; its "
+               "equilibrium is 1e5-1e7 steps away, so every request ends at the cap)",
+    "reference_plane": "clean bubble (beta = 0) on the reference-temperature plane, the SRF "
+                       "equilibrium: requests end when the start-up flow has decayed below "
+                       "tol for t* = R/U_o",
+}
 
 
 def run_e2e(args, lbm, torch, stream, params) -> dict:
@@ -675,15 +692,13 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=500,
                     help="requests of the served workload (0: skip it)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--serve-max-steps", type=int, default=4000,
-                    help="step cap of a served request (its terminal state is usually "
-                         "10^5-10^6 steps away; see the served block's converged count)")
+    ap.add_argument("--serve-max-steps", type=int, default=200000,
+                    help="step cap of the served run to terminal state")
+    ap.add_argument("--serve-throughput-steps", type=int, default=4000,
+                    help="step cap of the served run over the full lattice range (0: skip)")
     ap.add_argument("--serve-round-steps", type=int, default=128)
-    ap.add_argument("--serve-nx-max", type=int, default=512)
-    ap.add_argument("--serve-start", default="quarter", choices=["quarter", "reference_plane"],
-                    help="quarter: the bubble a quarter of the way along the channel (the "
-                         "configured stream); reference_plane: a clean bubble on the "
-                         "reference-temperature plane, which reaches its terminal state")
+    ap.add_argument("--serve-nx-max", type=int, default=128,
+                    help="largest nx of the served run to terminal state")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
