@@ -484,12 +484,12 @@ def run_gpu(args) -> None:
     value = weak_scaling_value(ms_max, nodes_per_step, args.steps, ws)
 
     # roofline of the dominant kernel: every launch in the timed region is a
-    # fused step kernel (one simulation, or every simulation of the batch that
-    # the kernel family takes, per launch)
+    # fused step kernel (one simulation, or as many simulations of the batch
+    # as one launch of the kernel family takes), so the algorithmic bytes of
+    # one launch are those of all timed steps over the launch count
     per_launch_ms = ms / launches
-    sims_per_launch = len(params) if args.mode == "batched" else 1
     bpn = BYTES_PER_NODE_STEP[args.precision]
-    per_launch_bytes = bpn * nodes_per_step / len(params) * sims_per_launch
+    per_launch_bytes = bpn * nodes_per_step * args.steps / launches
     peaks = measured_peaks()
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
     kernel = step_kernel_name(args.mode, args.precision, params)

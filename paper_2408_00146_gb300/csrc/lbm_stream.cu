@@ -793,57 +793,96 @@ struct Stage16 {
             "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(x), "r"(y), "r"(bar)
             : "memory");
     }
-    // rest-state moments of local column c (-8 <= c < 40), chunk row rr (-1 .. 8)
-    __device__ __forceinline__ float4 mom_at(int st, int c, int rr) const
+    // Rest-state moments in a stage: six groups of eight columns, rows -1 .. 8
+    // of the chunk.  A node's float4 sits at byte offset own (local column c,
+    // -8 <= c < 40; chunk row rr, -1 .. 8); its x neighbours are 16 bytes
+    // away within a group and one group minus seven columns away across a
+    // group boundary, so the nine sources of a node are three base offsets
+    // and immediate row offsets.
+    static constexpr int kMomRow = 8 * 16;
+    static constexpr int kMomGroup = (kTileY + 2) * kMomRow;
+    struct MomAddr {
+        int own, east, west;   // byte offsets of (c, rr), (c + 1, rr), (c - 1, rr)
+    };
+    __device__ __forceinline__ static MomAddr mom_addr(int c, int rr)
     {
-        return sm.mom[st][(c + 8) >> 3][rr + 1][(c + 8) & 7];
+        const int cc = c + 8, i = cc & 7;
+        MomAddr m;
+        m.own = (cc >> 3) * kMomGroup + (rr + 1) * kMomRow + i * 16;
+        m.east = m.own + (i == 7 ? kMomGroup - 7 * 16 : 16);
+        m.west = m.own - (i == 0 ? kMomGroup - 7 * 16 : 16);
+        return m;
+    }
+    __device__ __forceinline__ const char* mom_base(int st) const
+    {
+        return reinterpret_cast<const char*>(&sm.mom[st][0][0][0]);
+    }
+    // the float4 of the node a population of direction (ex, ey) came from
+    template <int ex, int ey>
+    __device__ __forceinline__ static float4 mom_src(const char* base, const MomAddr& m)
+    {
+        const int o = ex > 0 ? m.west : (ex < 0 ? m.east : m.own);
+        return *reinterpret_cast<const float4*>(base + o - ey * kMomRow);
     }
     // The differences t_a = f_a - k_a r of a node's populations, r its own rest
     // value: f_a = k_a m(src_a) + dev_a with src_a the node the population came
     // from (itself where it bounced off a wall), so t_a = k_a (m(src_a) - r) +
     // dev_a, exact up to the rounding of that small sum.  Direction by
     // direction: one float4 load (four sets) per source node, and the sums
-    // accumulated in the order a = 0..8 (sum_seq), which every evaluation of a
-    // node's fields shares.
-    template <int NSET, int SET0, class Dev, class Acc>
-    __device__ __forceinline__ void diffs16(int st, int c, int rr, int phys, const Dev& dev,
-                                            float4 m0, const Acc& acc) const
+    // accumulated in the order a = 0..8, which every evaluation of a node's
+    // fields shares.  rest(m4, k) picks the rest value of the k-th set taken
+    // from a float4; WALL: the row may be next to a wall (bot, top).
+    template <int NSET, bool WALL, class Dev, class Rest, class Acc>
+    __device__ __forceinline__ static void diffs16(const char* base, const MomAddr& ma, bool bot,
+                                                   bool top, const Dev& dev, float4 m0,
+                                                   const Rest& rest, const Acc& acc)
     {
-        const bool bot = d.walls && phys == 1, top = d.walls && phys == d.ny - 2;
-        const float r[4] = {m0.x, m0.y, m0.z, m0.w};
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            const int ex = ex_dir(a), ey = ey_dir(a);
-            const bool own = a == 0 || (ey > 0 && bot) || (ey < 0 && top);
-            const float4 m4 = own ? m0 : mom_at(st, c - ex, rr - ey);
-            const float ms[4] = {m4.x, m4.y, m4.z, m4.w};
-#pragma unroll
-            for (int k = 0; k < NSET; ++k) {
-                const int set = SET0 + k;
-                acc(k, a, fmaf(k_of_dir(a), ms[set] - r[set], s2f<T16>(dev(9 * set + a))));
+            float4 m4 = m0;
+            switch (a) {   // (a is a constant once the loop is unrolled)
+            case 1: m4 = mom_src<1, 0>(base, ma); break;
+            case 2: m4 = mom_src<0, 1>(base, ma); break;
+            case 3: m4 = mom_src<-1, 0>(base, ma); break;
+            case 4: m4 = mom_src<0, -1>(base, ma); break;
+            case 5: m4 = mom_src<1, 1>(base, ma); break;
+            case 6: m4 = mom_src<-1, 1>(base, ma); break;
+            case 7: m4 = mom_src<-1, -1>(base, ma); break;
+            case 8: m4 = mom_src<1, -1>(base, ma); break;
+            default: break;
             }
+            if (WALL) {
+                const int ey = ey_dir(a);
+                if ((ey > 0 && bot) || (ey < 0 && top)) m4 = m0;
+            }
+#pragma unroll
+            for (int k = 0; k < NSET; ++k)
+                acc(k, a, fmaf(k_of_dir(a), rest(m4, k) - rest(m0, k), s2f<T16>(dev(k, a))));
         }
     }
-    template <class Dev>
-    __device__ __forceinline__ Mom rebuild_moments(int st, int c, int rr, int phys,
-                                                   const Dev& dev) const
+    template <bool WALL, class Dev>
+    __device__ __forceinline__ Mom rebuild_moments(const char* base, const MomAddr& ma, bool bot,
+                                                   bool top, const Dev& dev) const
     {
-        const float4 m0 = mom_at(st, c, rr);
+        const float4 m0 = *reinterpret_cast<const float4*>(base + ma.own);
         SetMom sm4[4];
         float gnd = 0.0f, gxy = 0.0f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) sm4[k] = SetMom{0.0f, 0.0f, 0.0f, 0.0f};
-        diffs16<4, 0>(st, c, rr, phys, dev, m0, [&](int k, int a, float t) {
-            const int ex = ex_dir(a), ey = ey_dir(a);
-            sm4[k].d += t;
-            if (ex) sm4[k].jx += ex * t;
-            if (ey) sm4[k].jy += ey * t;
-            if (k == 1) {
-                if (ex != 0 && ey == 0) gnd += t;
-                if (ex == 0 && ey != 0) gnd -= t;
-                if (ex != 0 && ey != 0) gxy += (ex * ey) * t;
-            }
-        });
+        diffs16<4, WALL>(
+            base, ma, bot, top, [&](int k, int a) { return dev(9 * k + a); }, m0,
+            [](const float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); },
+            [&](int k, int a, float t) {
+                const int ex = ex_dir(a), ey = ey_dir(a);
+                sm4[k].d += t;
+                if (ex) sm4[k].jx += ex * t;
+                if (ey) sm4[k].jy += ey * t;
+                if (k == 1) {
+                    if (ex != 0 && ey == 0) gnd += t;
+                    if (ex == 0 && ey != 0) gnd -= t;
+                    if (ex != 0 && ey != 0) gxy += (ex * ey) * t;
+                }
+            });
         sm4[0].r = m0.x;
         sm4[1].r = m0.y;
         sm4[2].r = m0.z;
@@ -860,8 +899,18 @@ struct Stage16 {
     __device__ __forceinline__ Mom own_moments(int st, int rb, int tx, int phys) const
     {
         const T16* p = &sm.dev[st][0][rb][tx];
-        return rebuild_moments(st, tx, rb, phys, [&](int i) { return p[i * kTileY * kTileX]; });
+        const auto dev = [&](int i) { return p[i * kTileY * kTileX]; };
+        const MomAddr ma = mom_addr(tx, rb);
+        const char* base = mom_base(st);
+        // a warp is one row: the wall test is uniform across it
+        const bool bot = d.walls && phys == 1, top = d.walls && phys == d.ny - 2;
+        if (bot || top) return rebuild_moments<true>(base, ma, bot, top, dev);
+        return rebuild_moments<false>(base, ma, false, false, dev);
     }
+    // Side items: 0, 1: phi at the outer columns -2, w + 1; 2..5: the inner
+    // columns -1, w, set pair (f, g) or (h, q).  Every item takes the same
+    // two-set path (outer items use its first set), so that the lanes of a
+    // warp do not split over set pairs; only the field update differs.
     template <int SL>
     __device__ __forceinline__ void side_item(int st, int item, int r, int phys, int rw,
                                               Window<SL>& W) const
@@ -871,28 +920,26 @@ struct Stage16 {
         const int f = outer ? 0 : (item - 2) % 2;
         const int c = outer ? (lr ? sp.w + 1 : -2) : (lr ? sp.w : -1);
         const int bc = lr ? c - sp.w : c + 8;
-        const T16* p = &sm.side[st][lr][0][r][bc];
+        const T16* p = &sm.side[st][lr][18 * f][r][bc];
         constexpr int P = kTileY * 8;
-        const auto dev = [&](int i) { return p[i * P]; };
-        const float4 m0 = mom_at(st, c, r);
+        const MomAddr ma = mom_addr(c, r);
+        const char* base = mom_base(st);
+        const float4 m0 = *reinterpret_cast<const float4*>(base + ma.own);
+        const bool bot = d.walls && phys == 1, top = d.walls && phys == d.ny - 2;
+        float d1 = 0.0f, d2 = 0.0f;
+        diffs16<2, true>(
+            base, ma, bot, top, [&](int k, int a) { return p[(9 * k + a) * P]; }, m0,
+            [f](const float4& v, int k) { return k == 0 ? (f ? v.z : v.x) : (f ? v.w : v.y); },
+            [&](int k, int, float t) {
+                if (k == 0) d1 += t;
+                else d2 += t;
+            });
+        const float s1 = fmaf(36.0f, f ? m0.z : m0.x, d1);
         if (outer) {
-            float dd = 0.0f;
-            diffs16<1, 0>(st, c, r, phys, dev, m0, [&](int, int, float t) { dd += t; });
-            put_side_phi(d, W, rw, phys, c, fmaf(36.0f, m0.x, dd));
+            put_side_phi(d, W, rw, phys, c, s1);
             return;
         }
-        float d1 = 0.0f, d2 = 0.0f;
-        const auto acc2 = [&](int k, int, float t) {
-            if (k == 0) d1 += t;
-            else d2 += t;
-        };
-        if (f == 0) {
-            diffs16<2, 0>(st, c, r, phys, dev, m0, acc2);
-            put_side_pair(d, W, rw, phys, c, 1, fmaf(36.0f, m0.x, d1), fmaf(36.0f, m0.y, d2));
-        } else {
-            diffs16<2, 2>(st, c, r, phys, dev, m0, acc2);
-            put_side_pair(d, W, rw, phys, c, 2, fmaf(36.0f, m0.z, d1), fmaf(36.0f, m0.w, d2));
-        }
+        put_side_pair(d, W, rw, phys, c, f == 0 ? 1 : 2, s1, fmaf(36.0f, f ? m0.w : m0.y, d2));
     }
 };
 
