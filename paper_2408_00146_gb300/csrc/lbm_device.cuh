@@ -111,6 +111,14 @@ __device__ __forceinline__ void central_to_pop(float c00, float c10, float c01, 
 #undef XPASS
 }
 
+// Packed FP32 pairs: one FFMA2 / FADD2 / FMUL2 instruction does the
+// operation on both lanes, each lane rounded exactly as the scalar operation.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 __device__ __forceinline__ float sum9(const float v[9])
 {
     return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];

@@ -89,25 +89,43 @@ __device__ __forceinline__ float diffs32(const float f[9], float t[9])
     return r;
 }
 
+// The same sums over packed pairs of sets (one lane per set).
+__device__ __forceinline__ float2 sum_t2(const float2 t[9])
+{
+    return add2(add2(add2(add2(t[1], t[2]), add2(t[3], t[4])), add2(add2(t[5], t[6]), add2(t[7], t[8]))),
+                t[0]);
+}
+__device__ __forceinline__ float2 mx9_2(const float2 v[9])
+{
+    return add2(add2(sub2(v[1], v[3]), sub2(v[5], v[6])), sub2(v[8], v[7]));
+}
+__device__ __forceinline__ float2 my9_2(const float2 v[9])
+{
+    return sub2(add2(sub2(v[2], v[4]), add2(v[5], v[6])), add2(v[7], v[8]));
+}
+
+// The moments of a node's FP32 populations get(0 .. 35), sets in the packed
+// pairs (f, g) and (h, q); each lane as diffs32 and set_moments compute it.
 template <class Get>
 __device__ __forceinline__ Mom moments_of(const Get& get)
 {
     Mom m;
-    float v[9], t[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = get(a);
-    m.f = set_moments(diffs32(v, t), t);
+    for (int p = 0; p < 2; ++p) {
+        float2 v[9], t[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = get(9 + a);
-    m.g = set_moments(diffs32(v, t), t);
-    m.gnd = (t[1] + t[3]) - (t[2] + t[4]);
-    m.gxy = (t[5] + t[7]) - (t[6] + t[8]);
+        for (int a = 0; a < 9; ++a) v[a] = make_float2(get(18 * p + a), get(18 * p + 9 + a));
+        const float2 r = mul2(v[0], f2(0.0625f));
 #pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = get(18 + a);
-    m.h = set_moments(diffs32(v, t), t);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = get(27 + a);
-    m.q = set_moments(diffs32(v, t), t);
+        for (int a = 0; a < 9; ++a) t[a] = fma2(f2(-k_of_dir(a)), r, v[a]);
+        const float2 d = sum_t2(t), jx = mx9_2(t), jy = my9_2(t);
+        (p ? m.h : m.f) = SetMom{r.x, d.x, jx.x, jy.x};
+        (p ? m.q : m.g) = SetMom{r.y, d.y, jx.y, jy.y};
+        if (p == 0) {
+            m.gnd = (t[1].y + t[3].y) - (t[2].y + t[4].y);
+            m.gxy = (t[5].y + t[7].y) - (t[6].y + t[8].y);
+        }
+    }
     return m;
 }
 
@@ -828,11 +846,12 @@ struct Stage16 {
     // value: f_a = k_a m(src_a) + dev_a with src_a the node the population came
     // from (itself where it bounced off a wall), so t_a = k_a (m(src_a) - r) +
     // dev_a, exact up to the rounding of that small sum.  Direction by
-    // direction: one float4 load (four sets) per source node, and the sums
-    // accumulated in the order a = 0..8, which every evaluation of a node's
-    // fields shares.  rest(m4, k) picks the rest value of the k-th set taken
-    // from a float4; WALL: the row may be next to a wall (bot, top).
-    template <int NSET, bool WALL, class Dev, class Rest, class Acc>
+    // direction: one float4 load (four sets) per source node, the sets in
+    // packed pairs, and the sums accumulated in the order a = 0..8, which every
+    // evaluation of a node's fields shares.  rest(m4, p): the rest values of
+    // pair p from a float4; dev(p, a): the pair's two deviations of direction
+    // a; WALL: the row may be next to a wall (bot, top).
+    template <int NPAIR, bool WALL, class Dev, class Rest, class Acc>
     __device__ __forceinline__ static void diffs16(const char* base, const MomAddr& ma, bool bot,
                                                    bool top, const Dev& dev, float4 m0,
                                                    const Rest& rest, const Acc& acc)
@@ -856,8 +875,8 @@ struct Stage16 {
                 if ((ey > 0 && bot) || (ey < 0 && top)) m4 = m0;
             }
 #pragma unroll
-            for (int k = 0; k < NSET; ++k)
-                acc(k, a, fmaf(k_of_dir(a), rest(m4, k) - rest(m0, k), s2f<T16>(dev(k, a))));
+            for (int p = 0; p < NPAIR; ++p)
+                acc(p, a, fma2(f2(k_of_dir(a)), sub2(rest(m4, p), rest(m0, p)), dev(p, a)));
         }
     }
     template <bool WALL, class Dev>
@@ -865,33 +884,32 @@ struct Stage16 {
                                                    bool top, const Dev& dev) const
     {
         const float4 m0 = *reinterpret_cast<const float4*>(base + ma.own);
-        SetMom sm4[4];
-        float gnd = 0.0f, gxy = 0.0f;
+        float2 dd[2], jx[2], jy[2];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sm4[k] = SetMom{0.0f, 0.0f, 0.0f, 0.0f};
-        diffs16<4, WALL>(
-            base, ma, bot, top, [&](int k, int a) { return dev(9 * k + a); }, m0,
-            [](const float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); },
-            [&](int k, int a, float t) {
+        for (int p = 0; p < 2; ++p) dd[p] = jx[p] = jy[p] = f2(0.0f);
+        float gnd = 0.0f, gxy = 0.0f;
+        diffs16<2, WALL>(
+            base, ma, bot, top,
+            [&](int p, int a) { return make_float2(s2f<T16>(dev(18 * p + a)), s2f<T16>(dev(18 * p + 9 + a))); },
+            m0, [](const float4& v, int p) { return p == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w); },
+            [&](int p, int a, float2 t) {
                 const int ex = ex_dir(a), ey = ey_dir(a);
-                sm4[k].d += t;
-                if (ex) sm4[k].jx += ex * t;
-                if (ey) sm4[k].jy += ey * t;
-                if (k == 1) {
-                    if (ex != 0 && ey == 0) gnd += t;
-                    if (ex == 0 && ey != 0) gnd -= t;
-                    if (ex != 0 && ey != 0) gxy += (ex * ey) * t;
+                dd[p] = add2(dd[p], t);
+                if (ex > 0) jx[p] = add2(jx[p], t);
+                if (ex < 0) jx[p] = sub2(jx[p], t);
+                if (ey > 0) jy[p] = add2(jy[p], t);
+                if (ey < 0) jy[p] = sub2(jy[p], t);
+                if (p == 0) {
+                    if (ex != 0 && ey == 0) gnd += t.y;
+                    if (ex == 0 && ey != 0) gnd -= t.y;
+                    if (ex != 0 && ey != 0) gxy += (ex * ey) * t.y;
                 }
             });
-        sm4[0].r = m0.x;
-        sm4[1].r = m0.y;
-        sm4[2].r = m0.z;
-        sm4[3].r = m0.w;
         Mom m;
-        m.f = sm4[0];
-        m.g = sm4[1];
-        m.h = sm4[2];
-        m.q = sm4[3];
+        m.f = SetMom{m0.x, dd[0].x, jx[0].x, jy[0].x};
+        m.g = SetMom{m0.y, dd[0].y, jx[0].y, jy[0].y};
+        m.h = SetMom{m0.z, dd[1].x, jx[1].x, jy[1].x};
+        m.q = SetMom{m0.w, dd[1].y, jx[1].y, jy[1].y};
         m.gnd = gnd;
         m.gxy = gxy;
         return m;
@@ -926,14 +944,13 @@ struct Stage16 {
         const char* base = mom_base(st);
         const float4 m0 = *reinterpret_cast<const float4*>(base + ma.own);
         const bool bot = d.walls && phys == 1, top = d.walls && phys == d.ny - 2;
-        float d1 = 0.0f, d2 = 0.0f;
-        diffs16<2, true>(
-            base, ma, bot, top, [&](int k, int a) { return p[(9 * k + a) * P]; }, m0,
-            [f](const float4& v, int k) { return k == 0 ? (f ? v.z : v.x) : (f ? v.w : v.y); },
-            [&](int k, int, float t) {
-                if (k == 0) d1 += t;
-                else d2 += t;
-            });
+        float2 dd = f2(0.0f);
+        diffs16<1, true>(
+            base, ma, bot, top,
+            [&](int, int a) { return make_float2(s2f<T16>(p[a * P]), s2f<T16>(p[(9 + a) * P])); }, m0,
+            [f](const float4& v, int) { return f ? make_float2(v.z, v.w) : make_float2(v.x, v.y); },
+            [&](int, int, float2 t) { dd = add2(dd, t); });
+        const float d1 = dd.x, d2 = dd.y;
         const float s1 = fmaf(36.0f, f ? m0.z : m0.x, d1);
         if (outer) {
             put_side_phi(d, W, rw, phys, c, s1);
