@@ -64,20 +64,11 @@ struct Mom {
     float gnd, gxy;     // g: sum g (ex^2 - ey^2), sum g ex ey
 };
 
-// The moments of one set from its differences t[9] (fixed summation order,
-// shared by every place that evaluates a node).
+// The sum of one set's differences t[9] (fixed summation order, shared by
+// every place that evaluates a node).
 __device__ __forceinline__ float sum_t(const float t[9])
 {
     return (((t[1] + t[2]) + (t[3] + t[4])) + ((t[5] + t[6]) + (t[7] + t[8]))) + t[0];
-}
-__device__ __forceinline__ SetMom set_moments(float r, const float t[9])
-{
-    SetMom m;
-    m.r = r;
-    m.d = sum_t(t);
-    m.jx = mx9(t);
-    m.jy = my9(t);
-    return m;
 }
 
 // FP32 populations f[9] of one set: r = f_0 / 16.
@@ -105,7 +96,8 @@ __device__ __forceinline__ float2 my9_2(const float2 v[9])
 }
 
 // The moments of a node's FP32 populations get(0 .. 35), sets in the packed
-// pairs (f, g) and (h, q); each lane as diffs32 and set_moments compute it.
+// pairs (f, g) and (h, q): per lane r = f_0/16 and t_a as diffs32, d = sum_t,
+// j = (mx9, my9) of t.
 template <class Get>
 __device__ __forceinline__ Mom moments_of(const Get& get)
 {
