@@ -309,9 +309,16 @@ def workload_config(work: str, params: list[dict], precision: str) -> dict:
             "sims_per_gpu": len(params),
             "fluid_nodes_per_step": sum(fluid_nodes(p) for p in params),
             "physics": "density ratio 10, SRF quadratic law, Gibbs term (seeded synthetic)",
-            "l2": "working set %.0f MB > 129 MB L2; simulations interleaved per step"
-                  % (sum(2 * BYTES_PER_NODE_BUFFER[precision] * p["nx"] * p["ny"]
-                         for p in params) / 1e6)}
+            "l2": l2_note(params, precision)}
+
+
+def l2_note(params: list[dict], precision: str) -> str:
+    """Working set (both population buffers of every simulation) against the
+    129 MB L2: above it, every step streams its inputs from HBM."""
+    mb = sum(2 * BYTES_PER_NODE_BUFFER[precision] * p["nx"] * p["ny"] for p in params) / 1e6
+    if mb > 129.0:
+        return "working set %.0f MB > 129 MB L2; simulations interleaved per step" % mb
+    return "working set %.0f MB fits the 129 MB L2 (a profiling case, not a bench line)" % mb
 
 
 def run_reference(args) -> None:

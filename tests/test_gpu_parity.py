@@ -105,11 +105,25 @@ def test_channel_64x128_2000_steps(lbm, orc, noise):
     assert a["mass_psi"] == pytest.approx(b["mass_psi"], rel=1e-5)
 
 
+def _streams(nx, ny, walls, precision=0):
+    """Whether the streaming kernels take the lattice: nx >= 32 and a multiple
+    of 4 (FP32) or 8 (16-bit), at least 16 fluid rows, walls or (FP32) a
+    periodic y of whole 8-row chunks."""
+    nfy = ny - 2 if walls else ny
+    if nx % (4 if precision == 0 else 8) or nx < 32 or nfy < 16:
+        return False
+    return bool(walls) or (precision == 0 and nfy % 8 == 0)
+
+
 @pytest.mark.parametrize("nx,ny,walls", [(45, 37, 1), (37, 29, 0), (4, 5, 1), (4, 4, 0),
-                                         (33, 9, 1), (70, 19, 0)])
+                                         (33, 9, 1), (70, 19, 0),
+                                         # streaming: partial last column and chunk,
+                                         # a 4-wide last column, periodic y
+                                         (80, 63, 1), (36, 21, 1), (68, 24, 0), (40, 40, 0)])
 def test_ragged_and_minimal_lattices(lbm, orc, nx, ny, walls):
-    """Sizes that leave partial tiles in x and y, the smallest lattices the
-    ABI accepts, both boundary modes."""
+    """Sizes that leave partial tiles (or a partial last column and chunk of
+    the streaming kernel) in x and y, the smallest lattices the ABI accepts,
+    both boundary modes."""
     p = si.scaled_channel(nx, ny)
     # a bubble only where it can be resolved (R >= W); the smallest lattices
     # run bubble-free (a sub-width bubble makes n and kappa ill-conditioned:
@@ -120,6 +134,7 @@ def test_ragged_and_minimal_lattices(lbm, orc, nx, ny, walls):
         p.update(R=0.0, nu_A=0.0335, alpha_A=3.35e-3)
     f = si.parity_fields(p, seed=7)
     sim, o = _pair(lbm, orc, p, f)
+    assert (lbm.lbm_batch_plan([sim])[0] > 0) == _streams(nx, ny, walls)
     for n in (1, 29):
         sim.step(n)
         o.step(n)

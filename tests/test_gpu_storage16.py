@@ -1,8 +1,9 @@
 """16-bit population storage (lbm_params.precision = LBM_FP16 / LBM_BF16)
 against the FP64 oracle, through the C ABI.
 
-The populations are kept as FP32 rest-state moments M per node plus 16-bit
-deviations dev_a = f_a - w_a M(source).  The arithmetic stays FP32, so the
+The populations are kept as FP32 rest values m = M/36 per node (M the
+zeroth moment of the set) plus 16-bit deviations dev_a = f_a - k_a m(source)
+with the integer weights k_a = 36 w_a = 16, 4, 1.  The arithmetic stays FP32, so the
 errors below come from rounding the deviations: a relative 2^-11 (binary16)
 or 2^-8 (bfloat16) of each deviation per step.  Deviations are the
 velocity, flux and non-equilibrium content of a population (the conserved
@@ -129,9 +130,13 @@ def test_channel_64x128_2000_steps(lbm, orc, prec, noise):
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("nx,ny,walls", [(45, 37, 1), (37, 29, 0), (4, 5, 1), (4, 4, 0),
-                                         (33, 9, 1), (70, 19, 0)])
+                                         (33, 9, 1), (70, 19, 0),
+                                         # streaming: partial last column and chunk, an
+                                         # 8-wide last column; periodic y (tile kernel)
+                                         (80, 63, 1), (40, 21, 1), (40, 24, 0)])
 def test_ragged_and_minimal_lattices(lbm, orc, prec, nx, ny, walls):
-    """Partial tiles, the smallest lattices, both boundary modes, 30 steps.
+    """Partial tiles (or a partial last column and chunk of the streaming
+    kernel), the smallest lattices, both boundary modes, 30 steps.
     On the bubble-free lattices p and u are the seeded noise alone, so p is
     measured against rho_A max|u| as well as its own size."""
     p = si.scaled_channel(nx, ny)
@@ -143,6 +148,9 @@ def test_ragged_and_minimal_lattices(lbm, orc, prec, nx, ny, walls):
     f = si.parity_fields(p, seed=7)
     sim = lbm.Sim(p)
     sim.init(f)
+    nfy = ny - 2 if walls else ny
+    streams = nx % 8 == 0 and nx >= 32 and nfy >= 16 and bool(walls)
+    assert (lbm.lbm_batch_plan([sim])[0] > 0) == streams
     o = orc.Oracle(p)
     o.init_fields(f)
     sim.step(30)
