@@ -3,21 +3,22 @@ against the FP64 oracle, through the C ABI.
 
 The populations are kept as FP32 rest values m = M/36 per node (M the
 zeroth moment of the set) plus 16-bit deviations dev_a = f_a - k_a m(source)
-with the integer weights k_a = 36 w_a = 16, 4, 1.  The arithmetic stays FP32, so the
-errors below come from rounding the deviations: a relative 2^-11 (binary16)
-or 2^-8 (bfloat16) of each deviation per step.  Deviations are the
-velocity, flux and non-equilibrium content of a population (the conserved
-scalars ride in M), so the tolerances are stated per observable, measured
-against each field's magnitude (velocities against the velocity scale):
+with the integer weights k_a = 36 w_a = 16, 4, 1.  The arithmetic stays
+FP32, so the errors below come from rounding the deviations: a relative
+2^-11 (binary16) or 2^-8 (bfloat16) of each deviation per step.  Deviations
+are the velocity, flux and non-equilibrium content of a population (the
+conserved scalars ride in m), so the tolerances are stated per observable,
+measured against each field's magnitude (velocities against the velocity
+scale U_o of Eq. (21)):
 
   field        binary16   bfloat16   (max error after the 2000 steps of the
-  phi          3e-4       2e-3        64x128 channel; measured 6e-5-1e-4
-  u / U_o      1e-2       3e-2        and 5e-4 phi, 2e-3 and 8e-3 u, 3e-3
-  p            1e-2       5e-2        and 2e-2 p, 2e-5 and 1e-4 T, 3e-5-9e-5
-  T            1e-4       5e-4        and 2e-4 psi)
-  psi          3e-4       1e-3
+  phi          3e-4       2e-3        64x128 channel; measured 9e-5-1.3e-4
+  u / U_o      1e-2       3e-2        and 4.6e-4-5.3e-4 phi, 2.4e-3 and
+  p            1e-2       5e-2        8.7e-3 u, 3.8e-3 and 1.9e-2 p, 2.3e-5
+  T            1e-4       5e-4        and 1.1e-4 T, 3e-5-1.5e-4 and 2.1e-4
+  psi          3e-4       1e-3        psi)
 
-and the bubble centroid within 0.5 % of R (measured 2e-4 lu binary16, 1e-3
+and the bubble centroid within 0.5 % of R (measured 5e-4 lu binary16, 8e-4
 lu bfloat16 at R = 12)."""
 import numpy as np
 import pytest
