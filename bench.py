@@ -415,6 +415,11 @@ class Batch:
             s.close()
 
 
+def tile_shapes(lbm, sims) -> list[str]:
+    """The streaming tile shapes (columns x chunk rows) of a batch's plan."""
+    return sorted({f"{w}x{h}" for w, h in lbm.lbm_batch_tiles(sims) if w})
+
+
 def launch_mode(mode, steps, per_step, graph):
     """How the timed steps were issued: graphs replay only for runs of 64
     steps in one call."""
@@ -446,6 +451,7 @@ def sub_measure(lbm, torch, dev_index, params, precision, mode, steps, tune_step
            "achieved_gbs": gbs, "hbm_frac": gbs / peak,
            "bytes_per_node_step": BYTES_PER_NODE_STEP[precision],
            "strip_chunks": sorted(set(lbm.lbm_batch_plan(b.sims)) - {0}),
+           "tile_shapes": tile_shapes(lbm, b.sims),
            "clocks": {"sm_mhz": c["sm_mhz"], "reasons": c["reasons"], "samples": c["samples"]}}
     b.close()
     return out
@@ -477,6 +483,7 @@ def run_gpu(args) -> None:
     if args.mode == "batched":
         batch.tune(args.tune_steps)
     plan = lbm.lbm_batch_plan(batch.sims)
+    tiles = tile_shapes(lbm, batch.sims)
     warmup_run = args.warmup
     if args.mode == "batched" and not args.per_step_calls and args.steps >= 64:
         # at least one 64-step run, so that the batch's graph is captured
@@ -561,7 +568,8 @@ def run_gpu(args) -> None:
                     "other_mode": other,
                     "strip_plan": {"tuned": batch.tuned_steps > 0,
                                    "tuning_steps": batch.tuned_steps,
-                                   "strip_chunks": sorted(set(plan) - {0})},
+                                   "strip_chunks": sorted(set(plan) - {0}),
+                                   "tile_shapes": tiles},
                     "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
@@ -598,7 +606,8 @@ def run_served(args, torch, start: str, nx_max: int, max_steps: int,
     reqs = requests_from_stream(stream, max_steps=max_steps, tol=1e-6)
     free, _total = torch.cuda.mem_get_info()
     budget = int(min(150e9, 0.8 * free))
-    srv = Server(LbmEngine(), budget_bytes=budget, round_steps=args.serve_round_steps)
+    engine = LbmEngine()
+    srv = Server(engine, budget_bytes=budget, round_steps=args.serve_round_steps)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res = srv.run(reqs)
@@ -612,6 +621,7 @@ def run_served(args, torch, start: str, nx_max: int, max_steps: int,
                 "fp16_requests": sum(p["precision"] == 1 for _, p in stream),
                 "lattices": f"nx log-uniform 64..{nx_max} (x16), ny = 4 nx",
                 "start": START_NOTE[start],
+                "tile_shapes": sorted(f"{w}x{h}" for w, h in engine.tiles),
                 "vs_plain": out["mlups"] / plain_value if plain_value else None})
     return out
 

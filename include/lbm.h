@@ -201,18 +201,41 @@ lbm_status lbm_step(lbm_sim* sim, int64_t nsteps);
 lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps);
 
 /* Strip plan of a batch.  Sims eligible for the streaming kernels (see
- * lbm_step) are stepped by blocks that each walk one column of up to 32
- * nodes over a strip of chunks of 8 rows.  strip_chunks[i] (caller's array of
- * n) receives the strip length, in chunks, that lbm_step_batch uses for
- * sims[i] in this batch (0 for sims stepped by a tile kernel).  Without
- * tuning it comes from a cost model of each streaming launch (one strip per
- * block slot, resident blocks x SMs slots, longest first).  Host only; arguments as lbm_step_batch.  The
+ * lbm_step) are stepped by blocks of 256 threads that each walk one column of
+ * up to W nodes over a strip of chunks of H rows, in one of two compiled tile
+ * shapes W x H: 32 x 8, or 64 x 4 for FP32 storage (lbm_batch_tiles).  strip_chunks[i]
+ * (caller's array of n) receives the strip length, in chunks, that
+ * lbm_step_batch uses for sims[i] in this batch (0 for sims stepped by a tile
+ * kernel).  Without tuning it comes from a cost model of each streaming
+ * launch in the 32 x 8 shape (one strip per block slot, resident blocks x SMs
+ * slots, longest first).  Host only; arguments as lbm_step_batch.  The
  * paper has no counterpart (it fixes no GPU work decomposition).  Errors:
  * LBM_EINVAL, LBM_ESTATE. */
 lbm_status lbm_batch_plan(lbm_sim* const* sims, int32_t n, int32_t* strip_chunks);
 
+/* Tile shape of the batch's plan: tile_w[i] and tile_h[i] (caller's arrays of
+ * n; either may be NULL) receive the column width W and chunk height H of the
+ * streaming launch that steps sims[i] (0 for sims stepped by a tile kernel).
+ * Every sim of one streaming launch has the same shape.  Host only;
+ * arguments as lbm_step_batch.  The paper has no counterpart.  Errors:
+ * LBM_EINVAL, LBM_ESTATE. */
+lbm_status lbm_batch_tiles(lbm_sim* const* sims, int32_t n, int32_t* tile_w, int32_t* tile_h);
+
+/* Sets the plan of a batch, as lbm_tune_batch would after measuring it:
+ * tile_w[i] (32, or 64 for FP32 storage) and strip_chunks[i] (>= 4 chunks) for every sim the
+ * streaming kernels step (entries of the others are ignored); the sims of one
+ * streaming launch (one storage precision, see lbm_step_batch) must share a
+ * tile width.  Kept for later lbm_step_batch calls on sims of the same sizes
+ * in the same order on this host thread.  The result of a step does not
+ * depend on the plan.  Host only.  The paper has no counterpart.  Errors:
+ * LBM_EINVAL (NULL arrays, unknown width, strip_chunks < 4, mixed widths in
+ * one launch, batch arguments), LBM_ESTATE. */
+lbm_status lbm_pin_batch_plan(lbm_sim* const* sims, int32_t n, const int32_t* tile_w,
+                              const int32_t* strip_chunks);
+
 /* Measured choice of the strip plan of a batch (autotuner).  For each
- * distinct plan among the candidate strip lengths (the cost model's first),
+ * distinct plan among the tile shapes and candidate strip lengths (the cost
+ * model's first),
  * advances the whole batch trial_steps steps and times them with CUDA events
  * on the batch's stream; the fastest plan is kept and used by later
  * lbm_step_batch calls on sims of the same sizes in the same order, on this

@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
 SOURCES = ["lbm_kernels.cu", "lbm_stream.cu", "lbm_api.cu", "lbm_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "lbm_internal.h"), os.path.join(CSRC, "lbm_device.cuh"),
-           os.path.join(INCLUDE, "lbm.h")]
+           os.path.join(CSRC, "lbm_stream_body.cuh"), os.path.join(INCLUDE, "lbm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

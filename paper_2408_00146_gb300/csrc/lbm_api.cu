@@ -218,11 +218,16 @@ struct lbm_sim {
     double* h_res;   // pinned, 16 doubles
     int* err;        // device flag: a bounded wait in a kernel gave up
     bool have_tmap;  // TMA descriptors of both population buffers are valid
-    CUtensorMap tmap[2];   // populations (FP32) or deviations (16-bit), box {kTileX, 8, 36}
+    CUtensorMap tmap[2];   // FP32 tile kernels: populations, box {kTileX, kTileY, 36}
     bool ystream;    // steps use a streaming kernel (stream_eligible, descriptors valid)
-    CUtensorMap tside[2];  // side columns: box {4, 8, 36} (FP32) or {8, 8, 36} (16-bit)
-    CUtensorMap tmom[2];   // 16-bit storage: rest-state moments, box {4, 8, 10}
-    int strip_chunks;  // chunks per strip when stepped alone
+    // streaming kernels, per tile shape (W x H = kStreamW x kStreamH): the
+    // chunk (box {W, H, 36} of populations or deviations), the side columns
+    // (box {4, H, 36} FP32, {8, H, 36} 16-bit), the rest-state moments
+    // (16-bit: box {4, 8, H + 2})
+    CUtensorMap smap[kStreamShapes][2];
+    CUtensorMap sside[kStreamShapes][2];
+    CUtensorMap smom[kStreamShapes][2];
+    int plan;        // plan code (tile shape and strip length) when stepped alone
     cudaEvent_t obs_event;  // recorded after the last enqueued observation's copy
     bool obs_pending;       // an observation was enqueued (h_res is or will be valid)
     int64_t obs_t;          // the step count it observes
@@ -238,12 +243,13 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // TMA descriptors of both population buffers.  FP32: the populations
-// [36][ny][nx], box {kTileX, 8, 36} (tile and streaming kernels) and the
-// streaming kernel's side box {4, 8, 36}; TMA needs 16-byte row strides,
-// nx % 4 == 0.  16-bit storage: the deviations [36][ny][nx] (boxes {kTileX, 8,
-// 36} and {8, 8, 36}; nx % 8 == 0) and the rest-state moments, the float4
-// array [ny][nx] viewed as [ny][nx][4] floats (box {4, 8, 10}).  Without
-// them every step takes the tile kernels, which stage with plain loads.
+// [36][ny][nx] for the tile kernels (box {kTileX, kTileY, 36}); for each
+// streaming tile shape W x H the chunk box {W, H, 36} and the side box
+// {4, H, 36}; TMA needs 16-byte row strides, nx % 4 == 0.  16-bit storage:
+// the deviations [36][ny][nx] (boxes {W, H, 36} and {8, H, 36}; nx % 8 == 0)
+// and the rest-state moments, the float4 array [ny][nx] viewed as
+// [ny][nx][4] floats (box {4, 8, H + 2}).  Without them every step takes the
+// tile kernels, which stage with plain loads.
 bool encode_population_maps(lbm_sim* s)
 {
     const bool fp32 = s->p.precision == LBM_FP32;
@@ -259,26 +265,32 @@ bool encode_population_maps(lbm_sim* s)
     const CUtensorMapDataType dt = fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     const cuuint64_t dims[3] = {(cuuint64_t)s->p.nx, (cuuint64_t)s->p.ny, 36};
     const cuuint64_t strides[2] = {(cuuint64_t)s->p.nx * esz, (cuuint64_t)s->p.nx * s->p.ny * esz};
-    const cuuint32_t box[3] = {(cuuint32_t)kTileX, (cuuint32_t)kTileY, 36};
     const cuuint32_t estride[3] = {1, 1, 1};
-    const cuuint32_t side_box[3] = {fp32 ? 4u : 8u, (cuuint32_t)kTileY, 36};
     const cuuint64_t mdims[3] = {4, (cuuint64_t)s->p.nx, (cuuint64_t)s->p.ny};
     const cuuint64_t mstrides[2] = {4 * sizeof(float), (cuuint64_t)s->p.nx * 4 * sizeof(float)};
-    const cuuint32_t mbox[3] = {4, 8, (cuuint32_t)kTileY + 2};
+    auto enc = [&](CUtensorMap* m, CUtensorMapDataType type, void* base, const cuuint64_t* d,
+                   const cuuint64_t* st, const cuuint32_t* box) {
+        return encode(m, type, 3, base, d, st, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
     for (int b = 0; b < 2; ++b) {
-        CUresult r = encode(&s->tmap[b], dt, 3, s->pop[b], dims, strides, box, estride,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return false;
-        r = encode(&s->tside[b], dt, 3, s->pop[b], dims, strides, side_box, estride,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return false;
-        if (fp32) continue;
-        r = encode(&s->tmom[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->mom[b], mdims, mstrides,
-                   mbox, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return false;
+        if (fp32) {
+            const cuuint32_t box[3] = {(cuuint32_t)kTileX, (cuuint32_t)kTileY, 36};
+            if (!enc(&s->tmap[b], dt, s->pop[b], dims, strides, box)) return false;
+        }
+        for (int sh = 0; sh < kStreamShapes; ++sh) {
+            if (!stream_shape_available(sh, s->p.precision)) continue;
+            const cuuint32_t H = (cuuint32_t)kStreamH[sh];
+            const cuuint32_t box[3] = {(cuuint32_t)kStreamW[sh], H, 36};
+            const cuuint32_t side_box[3] = {fp32 ? 4u : 8u, H, 36};
+            if (!enc(&s->smap[sh][b], dt, s->pop[b], dims, strides, box)) return false;
+            if (!enc(&s->sside[sh][b], dt, s->pop[b], dims, strides, side_box)) return false;
+            if (fp32) continue;
+            const cuuint32_t mbox[3] = {4, 8, H + 2};
+            if (!enc(&s->smom[sh][b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, s->mom[b], mdims, mstrides, mbox))
+                return false;
+        }
     }
     return true;
 }
@@ -305,11 +317,18 @@ std::vector<int> candidate_lengths(int maxch)
     return out;
 }
 
-void plan_for_length(const int* nch, int n, int L, int* plan)
+// A streaming sim's plan, packed in one int: the tile shape (index into
+// kStreamW / kStreamH) and the strip length in chunks.
+constexpr int kShapeCode = 1 << 20;
+int plan_code(int shape, int chunks) { return shape * kShapeCode + chunks; }
+int plan_chunks(int code) { return code % kShapeCode; }
+int plan_shape(int code) { return code / kShapeCode; }
+
+void plan_for_length(const int* nch, int n, int L, int shape, int* plan)
 {
     for (int i = 0; i < n; ++i) {
         const int ns = (nch[i] + L - 1) / L;
-        plan[i] = std::max(4, (nch[i] + ns - 1) / ns);
+        plan[i] = plan_code(shape, std::max(4, (nch[i] + ns - 1) / ns));
     }
 }
 
@@ -322,9 +341,10 @@ double predicted_span(const int* nch, const int* ncol, int n, const int* plan, i
 {
     std::vector<int> lens;
     for (int i = 0; i < n; ++i) {
-        const int per_col = (nch[i] + plan[i] - 1) / plan[i];
+        const int L = plan_chunks(plan[i]);
+        const int per_col = (nch[i] + L - 1) / L;
         for (int c = 0; c < ncol[i]; ++c)
-            for (int t = 0; t < per_col; ++t) lens.push_back(std::min(plan[i], nch[i] - t * plan[i]));
+            for (int t = 0; t < per_col; ++t) lens.push_back(std::min(L, nch[i] - t * L));
     }
     std::sort(lens.begin(), lens.end(), std::greater<int>());
     std::vector<double> load(slots, 0.0);
@@ -339,41 +359,50 @@ double predicted_span(const int* nch, const int* ncol, int n, const int* plan, i
     return span;
 }
 
-// Plans by list of lattice sizes (chunks and columns, in launch-group
+// Plans (codes) by list of lattice sizes (nx and fluid rows, in launch-group
 // order), since lbm_step_batch may be called once per step.  A plan measured
 // by lbm_tune_batch (tuned) replaces the model's and is evicted last.
 struct PlanEntry {
     int n = -1, sms = 0, precision = 0;
     bool tuned = false;
-    int nchunks[kMaxBatch], ncol[kMaxBatch], plan[kMaxBatch];
+    int nx[kMaxBatch], nfy[kMaxBatch], plan[kMaxBatch];
 };
 constexpr int kPlanCache = 16;
 thread_local PlanEntry plan_cache[kPlanCache];
 thread_local int plan_next = 0;
 
-void plan_key(const LbmDev* const* devs, int n, int* nch, int* ncol)
+void plan_key(const LbmDev* const* devs, int n, int* nx, int* nfy)
 {
     for (int i = 0; i < n; ++i) {
-        nch[i] = (devs[i]->nfy + kTileY - 1) / kTileY;
-        ncol[i] = stream_columns(*devs[i]);
+        nx[i] = devs[i]->nx;
+        nfy[i] = devs[i]->nfy;
     }
 }
 
-PlanEntry* find_plan(const int* nch, const int* ncol, int n, int sms, int precision)
+// chunks and columns of each lattice in the tile shape
+void shape_counts(const LbmDev* const* devs, int n, int shape, int* nch, int* ncol)
+{
+    for (int i = 0; i < n; ++i) {
+        nch[i] = stream_chunks(*devs[i], shape);
+        ncol[i] = stream_columns(*devs[i], shape);
+    }
+}
+
+PlanEntry* find_plan(const int* nx, const int* nfy, int n, int sms, int precision)
 {
     for (PlanEntry& e : plan_cache) {
         if (e.n != n || e.sms != sms || e.precision != precision) continue;
         bool same = true;
-        for (int i = 0; i < n && same; ++i) same = e.nchunks[i] == nch[i] && e.ncol[i] == ncol[i];
+        for (int i = 0; i < n && same; ++i) same = e.nx[i] == nx[i] && e.nfy[i] == nfy[i];
         if (same) return &e;
     }
     return nullptr;
 }
 
-void store_plan(const int* nch, const int* ncol, int n, int sms, int precision, const int* plan,
+void store_plan(const int* nx, const int* nfy, int n, int sms, int precision, const int* plan,
                 bool tuned)
 {
-    PlanEntry* e = find_plan(nch, ncol, n, sms, precision);
+    PlanEntry* e = find_plan(nx, nfy, n, sms, precision);
     if (!e) {
         // round robin, passing over tuned entries while an untuned one is left
         for (int k = 0; k < kPlanCache && !e; ++k) {
@@ -392,27 +421,30 @@ void store_plan(const int* nch, const int* ncol, int n, int sms, int precision, 
     e->sms = sms;
     e->precision = precision;
     e->tuned = tuned;
-    std::memcpy(e->nchunks, nch, sizeof(int) * n);
-    std::memcpy(e->ncol, ncol, sizeof(int) * n);
+    std::memcpy(e->nx, nx, sizeof(int) * n);
+    std::memcpy(e->nfy, nfy, sizeof(int) * n);
     std::memcpy(e->plan, plan, sizeof(int) * n);
 }
 
 // The plan lbm_step_batch uses: a cached one (tuned or predicted), else the
-// candidate with the shortest predicted launch.  When even one strip per
-// column needs more than one wave of block slots, only strips of at most 16
-// chunks are considered: measured on the 64-channel ensemble, longer strips
-// in a multi-wave launch lose more to L2 misses of the side boxes (their
-// neighbouring columns run at other times) than they save in start-up.
+// candidate with the shortest predicted launch in the first tile shape (the
+// other shapes are tried by lbm_tune_batch, which measures).  When even one
+// strip per column needs more than one wave of block slots, only strips of at
+// most 16 chunks are considered: measured on the 64-channel ensemble, longer
+// strips in a multi-wave launch lose more to L2 misses of the side boxes
+// (their neighbouring columns run at other times) than they save in start-up.
 constexpr int kMultiWaveMaxStrip = 16;
 
 void plan_strips(const LbmDev* const* devs, int n, int num_sms, int precision, int* out)
 {
-    int nch[kMaxBatch], ncol[kMaxBatch];
-    plan_key(devs, n, nch, ncol);
-    if (const PlanEntry* e = find_plan(nch, ncol, n, num_sms, precision)) {
+    int nx[kMaxBatch], nfy[kMaxBatch], nch[kMaxBatch], ncol[kMaxBatch];
+    plan_key(devs, n, nx, nfy);
+    if (const PlanEntry* e = find_plan(nx, nfy, n, num_sms, precision)) {
         std::memcpy(out, e->plan, sizeof(int) * n);
         return;
     }
+    const int shape = 0;
+    shape_counts(devs, n, shape, nch, ncol);
     const int maxch = std::max(1, *std::max_element(nch, nch + n));
     const int slots = stream_blocks_per_sm(precision) * std::max(num_sms, 1);
     long long cols = 0;
@@ -422,14 +454,14 @@ void plan_strips(const LbmDev* const* devs, int n, int num_sms, int precision, i
     int best_plan[kMaxBatch], plan[kMaxBatch];
     for (int L : candidate_lengths(maxch)) {
         if (multi_wave && L > kMultiWaveMaxStrip) continue;
-        plan_for_length(nch, n, L, plan);
+        plan_for_length(nch, n, L, shape, plan);
         const double span = predicted_span(nch, ncol, n, plan, slots);
         if (span < best - 1e-9) {
             best = span;
             std::memcpy(best_plan, plan, sizeof(int) * n);
         }
     }
-    store_plan(nch, ncol, n, num_sms, precision, best_plan, false);
+    store_plan(nx, nfy, n, num_sms, precision, best_plan, false);
     std::memcpy(out, best_plan, sizeof(int) * n);
 }
 
@@ -493,7 +525,7 @@ static lbm_status create_impl(const lbm_params* p, void* stream, void* ws, size_
         if (e == cudaSuccess) e = prepare_stream();
         s->num_sms = sms > 0 ? sms : 1;
         const LbmDev* one = &s->dev;
-        plan_strips(&one, 1, s->num_sms, p->precision, &s->strip_chunks);
+        plan_strips(&one, 1, s->num_sms, p->precision, &s->plan);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s->h_res), 16 * sizeof(double));
@@ -585,48 +617,52 @@ static lbm_status ensure_stage(lbm_sim* s)
     return LBM_OK;
 }
 
-// Entry i of a streaming launch: sim s stepping from buffer `from`.
-static void stream_entry(StreamBatchArgs& a, int i, const lbm_sim* s, int from, int strip_chunks)
+// Entry i of a streaming launch in tile shape sh: sim s stepping from buffer
+// `from` with strips of L chunks.
+static void stream_entry(StreamBatchArgs& a, int i, const lbm_sim* s, int from, int sh, int L)
 {
-    a.tmap[i] = s->tmap[from];
-    a.tside[i] = s->tside[from];
+    a.tmap[i] = s->smap[sh][from];
+    a.tside[i] = s->sside[sh][from];
     a.dev[i] = s->dev;
     a.dst[i] = s->pop[from ^ 1];
     a.err[i] = s->err;
-    a.strip_chunks[i] = strip_chunks;
-    a.first[i + 1] = a.first[i] + stream_blocks(s->dev, strip_chunks);
+    a.strip_chunks[i] = L;
+    a.first[i + 1] = a.first[i] + stream_blocks(s->dev, L, sh);
 }
 
-static void stream16_entry(Stream16Args& a, int i, const lbm_sim* s, int from, int strip_chunks)
+static void stream16_entry(Stream16Args& a, int i, const lbm_sim* s, int from, int sh, int L)
 {
-    a.tmap[i] = s->tmap[from];
-    a.tside[i] = s->tside[from];
-    a.tmom[i] = s->tmom[from];
+    a.tmap[i] = s->smap[sh][from];
+    a.tside[i] = s->sside[sh][from];
+    a.tmom[i] = s->smom[sh][from];
     a.dev[i] = s->dev;
     a.dst[i] = s->pop[from ^ 1];
     a.mdst[i] = s->mom[from ^ 1];
     a.err[i] = s->err;
-    a.strip_chunks[i] = strip_chunks;
-    a.first[i + 1] = a.first[i] + stream_blocks(s->dev, strip_chunks);
+    a.strip_chunks[i] = L;
+    a.first[i + 1] = a.first[i] + stream_blocks(s->dev, L, sh);
 }
 
-// One streaming launch over sims[0 .. n-1] (one storage precision), each
-// from its current buffer with strip lengths plan[].
+// One streaming launch over sims[0 .. n-1] (one storage precision, one tile
+// shape), each from its current buffer with plan codes plan[].
 static cudaError_t launch_stream_group(lbm_sim* const* sims, int n, const int* plan, cudaStream_t st)
 {
     static thread_local StreamBatchArgs a32;  // ~27 KB each: kept off the stack
     static thread_local Stream16Args a16;
     const int precision = sims[0]->p.precision;
+    const int sh = plan_shape(plan[0]);
+    for (int i = 1; i < n; ++i)
+        if (plan_shape(plan[i]) != sh) return cudaErrorInvalidValue;
     if (precision == LBM_FP32) {
         a32.n = n;
         a32.first[0] = 0;
-        for (int i = 0; i < n; ++i) stream_entry(a32, i, sims[i], sims[i]->cur, plan[i]);
-        return launch_stream_batch(a32, st);
+        for (int i = 0; i < n; ++i) stream_entry(a32, i, sims[i], sims[i]->cur, sh, plan_chunks(plan[i]));
+        return launch_stream_batch(a32, sh, st);
     }
     a16.n = n;
     a16.first[0] = 0;
-    for (int i = 0; i < n; ++i) stream16_entry(a16, i, sims[i], sims[i]->cur, plan[i]);
-    return launch_stream16_batch(a16, precision, st);
+    for (int i = 0; i < n; ++i) stream16_entry(a16, i, sims[i], sims[i]->cur, sh, plan_chunks(plan[i]));
+    return launch_stream16_batch(a16, precision, sh, st);
 }
 
 // One step from buffer `from` to the other one, on stream st.
@@ -635,7 +671,7 @@ static cudaError_t step_once(lbm_sim* s, int from, cudaStream_t st)
     if (s->ystream) {
         const int cur = s->cur;
         s->cur = from;
-        cudaError_t e = launch_stream_group(&s, 1, &s->strip_chunks, st);
+        cudaError_t e = launch_stream_group(&s, 1, &s->plan, st);
         s->cur = cur;
         return e;
     }
@@ -1031,7 +1067,59 @@ lbm_status lbm_batch_plan(lbm_sim* const* sims, int32_t n, int32_t* strip_chunks
     if (st != LBM_OK) return st;
     static thread_local StreamLaunches SL;
     stream_launches(sims, n, SL);
-    for (int i = 0, k = 0; i < n; ++i) strip_chunks[i] = sims[i]->ystream ? SL.plan[SL.pos[k++]] : 0;
+    for (int i = 0, k = 0; i < n; ++i)
+        strip_chunks[i] = sims[i]->ystream ? plan_chunks(SL.plan[SL.pos[k++]]) : 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_tiles(lbm_sim* const* sims, int32_t n, int32_t* tile_w, int32_t* tile_h)
+{
+    lbm_status st = check_batch(sims, n, "lbm_batch_tiles");
+    if (st != LBM_OK) return st;
+    static thread_local StreamLaunches SL;
+    stream_launches(sims, n, SL);
+    for (int i = 0, k = 0; i < n; ++i) {
+        const int sh = sims[i]->ystream ? plan_shape(SL.plan[SL.pos[k++]]) : -1;
+        if (tile_w) tile_w[i] = sh < 0 ? 0 : kStreamW[sh];
+        if (tile_h) tile_h[i] = sh < 0 ? 0 : kStreamH[sh];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_pin_batch_plan(lbm_sim* const* sims, int32_t n, const int32_t* tile_w,
+                              const int32_t* strip_chunks)
+{
+    if (!tile_w || !strip_chunks) return fail(LBM_EINVAL, "tile_w or strip_chunks is NULL");
+    lbm_status st = check_batch(sims, n, "lbm_pin_batch_plan");
+    if (st != LBM_OK) return st;
+    static thread_local StreamLaunches SL;
+    stream_launches(sims, n, SL);
+    // plan codes in argument order of the streaming sims
+    int code[kMaxBatch];
+    for (int i = 0, k = 0; i < n; ++i) {
+        if (!sims[i]->ystream) continue;
+        int sh = -1;
+        for (int j = 0; j < kStreamShapes; ++j)
+            if (kStreamW[j] == tile_w[i]) sh = j;
+        if (sh < 0 || !stream_shape_available(sh, sims[i]->p.precision))
+            return fail(LBM_EINVAL, "tile_w[%d] = %d is not a compiled tile width for this storage",
+                        i, tile_w[i]);
+        if (strip_chunks[i] < 4) return fail(LBM_EINVAL, "strip_chunks[%d] < 4", i);
+        code[k++] = plan_code(sh, strip_chunks[i]);
+    }
+    for (int g = 0; g < SL.count; ++g) {
+        const int b = SL.begin[g], m = SL.begin[g + 1] - b;
+        int plan[kMaxBatch], nx[kMaxBatch], nfy[kMaxBatch];
+        const LbmDev* devs[kMaxBatch];
+        for (int i = 0; i < m; ++i) devs[i] = &SL.sims[b + i]->dev;
+        for (int a = 0; a < SL.sn; ++a)
+            if (SL.pos[a] >= b && SL.pos[a] < b + m) plan[SL.pos[a] - b] = code[a];
+        for (int i = 1; i < m; ++i)
+            if (plan_shape(plan[i]) != plan_shape(plan[0]))
+                return fail(LBM_EINVAL, "the sims of one streaming launch need one tile width");
+        plan_key(devs, m, nx, nfy);
+        store_plan(nx, nfy, m, SL.sims[b]->num_sms, SL.sims[b]->p.precision, plan, true);
+    }
     return LBM_OK;
 }
 
@@ -1060,16 +1148,20 @@ lbm_status lbm_tune_batch(lbm_sim* const* sims, int32_t n, int32_t trial_steps, 
     if (e == cudaSuccess) st = step_batch(sims, n, 1, arg_plan.data());
     for (int g = 0; g < SL.count && e == cudaSuccess && st == LBM_OK; ++g) {
         const int b = SL.begin[g], m = SL.begin[g + 1] - b;
-        int nch[kMaxBatch], ncol[kMaxBatch];
+        int nx[kMaxBatch], nfy[kMaxBatch], nch[kMaxBatch], ncol[kMaxBatch];
         const LbmDev* devs[kMaxBatch];
         for (int i = 0; i < m; ++i) devs[i] = &SL.sims[b + i]->dev;
-        plan_key(devs, m, nch, ncol);
-        // distinct plans of the candidate lengths, the model's first
+        plan_key(devs, m, nx, nfy);
+        // distinct plans of every tile shape and candidate length, the model's first
         std::vector<std::vector<int>> plans{std::vector<int>(SL.plan + b, SL.plan + b + m)};
         std::vector<int> plan(m);
-        for (int L : candidate_lengths(*std::max_element(nch, nch + m))) {
-            plan_for_length(nch, m, L, plan.data());
-            if (std::find(plans.begin(), plans.end(), plan) == plans.end()) plans.push_back(plan);
+        for (int sh = 0; sh < kStreamShapes; ++sh) {
+            if (!stream_shape_available(sh, SL.sims[b]->p.precision)) continue;
+            shape_counts(devs, m, sh, nch, ncol);
+            for (int L : candidate_lengths(*std::max_element(nch, nch + m))) {
+                plan_for_length(nch, m, L, sh, plan.data());
+                if (std::find(plans.begin(), plans.end(), plan) == plans.end()) plans.push_back(plan);
+            }
         }
         float best_ms = 0.0f;
         size_t best = 0;
@@ -1090,7 +1182,7 @@ lbm_status lbm_tune_batch(lbm_sim* const* sims, int32_t n, int32_t trial_steps, 
         }
         for (int i = 0; i < m; ++i) arg_plan[slot_to_arg[b + i]] = plans[best][i];
         if (e == cudaSuccess && st == LBM_OK)
-            store_plan(nch, ncol, m, SL.sims[b]->num_sms, SL.sims[b]->p.precision,
+            store_plan(nx, nfy, m, SL.sims[b]->num_sms, SL.sims[b]->p.precision,
                        plans[best].data(), true);
     }
     for (cudaEvent_t x : ev)

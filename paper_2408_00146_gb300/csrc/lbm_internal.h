@@ -94,14 +94,19 @@ cudaError_t launch_join_planes(const LbmDev& d, int precision, const void* dev, 
                                int a0, int count, float* planes, cudaStream_t s);
 
 // Streaming steps of up to kMaxBatch (FP32) or kMaxBatch16 (16-bit storage)
-// simulations per launch: blocks walk columns of up to kTileX nodes in +y
-// over strips of strip_chunks[s] 8-row chunks, reading the populations
-// through TMA descriptors of the source buffer: tmap[s] (box {kTileX, 8, 36})
-// and tside[s] (side columns: box {4, 8, 36} for FP32, {8, 8, 36} for 16-bit
-// deviations), and, with 16-bit storage, tmom[s] (rest-state moments, the
-// float4 array viewed as [ny][nx][4] floats, box {4, 8, 10}); first[] holds
-// the prefix sums of stream_blocks.  prepare_stream: per-device kernel
-// attributes, before the first launch.
+// simulations per launch, in one of kStreamShapes tile shapes: blocks of
+// 256 threads walk columns of up to kStreamW[shape] nodes in +y over strips
+// of strip_chunks[s] chunks of kStreamH[shape] rows, reading the populations
+// through TMA descriptors of the source buffer made for that shape: tmap[s]
+// (box {W, H, 36}) and tside[s] (side columns: box {4, H, 36} for FP32,
+// {8, H, 36} for 16-bit deviations), and, with 16-bit storage, tmom[s]
+// (rest-state moments, the float4 array viewed as [ny][nx][4] floats, box
+// {4, 8, H + 2}); first[] holds the prefix sums of stream_blocks.
+// prepare_stream: per-device kernel attributes, before the first launch.
+constexpr int kStreamShapes = 2;
+constexpr int kStreamW[kStreamShapes] = {32, 64};
+constexpr int kStreamH[kStreamShapes] = {8, 4};
+constexpr int kStreamBlocksPerSm = 2;
 struct StreamBatchArgs {
     CUtensorMap tmap[kMaxBatch];
     CUtensorMap tside[kMaxBatch];
@@ -129,16 +134,20 @@ static_assert(sizeof(StreamBatchArgs) <= 32764 && sizeof(Stream16Args) <= 32764,
               "kernel parameter limit");
 cudaError_t prepare_stream();
 // Whether a lattice of this storage precision can be stepped by the
-// streaming kernels: nx >= kTileX and a multiple of 4 (FP32) or 8 (16-bit:
-// 16-byte TMA rows), at least two chunks of fluid rows, and walls or (FP32
-// only) a periodic y axis of whole chunks.
+// streaming kernels: nx >= 32 and a multiple of 4 (FP32) or 8 (16-bit:
+// 16-byte TMA rows), at least 16 fluid rows, and walls or (FP32 only) a
+// periodic y axis of whole 8-row chunks.  The same lattices for every shape.
 bool stream_eligible(const LbmDev& d, int precision);
-int stream_columns(const LbmDev& d);
-// Resident blocks per SM of the streaming kernel of this precision.
+// Whether the tile shape has kernels for this storage precision (64 x 4:
+// FP32 only).
+bool stream_shape_available(int shape, int precision);
+int stream_columns(const LbmDev& d, int shape);
+int stream_chunks(const LbmDev& d, int shape);
+// Resident blocks per SM of the streaming kernels.
 int stream_blocks_per_sm(int precision);
-int stream_blocks(const LbmDev& d, int strip_chunks);
-cudaError_t launch_stream_batch(const StreamBatchArgs& args, cudaStream_t s);
-cudaError_t launch_stream16_batch(const Stream16Args& args, int precision, cudaStream_t s);
+int stream_blocks(const LbmDev& d, int strip_chunks, int shape);
+cudaError_t launch_stream_batch(const StreamBatchArgs& args, int shape, cudaStream_t s);
+cudaError_t launch_stream16_batch(const Stream16Args& args, int precision, int shape, cudaStream_t s);
 
 // Diagnostic: one block waits with the kernels' bounded wait (limit_ns) on a
 // barrier nothing completes and sets *flag = 1 when it gives up.

@@ -57,7 +57,7 @@ STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA"
 # Symbols include/lbm.h declares.
 EXPORTS = [
     "lbm_derive", "lbm_workspace_bytes", "lbm_create", "lbm_create_ex", "lbm_init", "lbm_step",
-    "lbm_step_batch", "lbm_batch_plan", "lbm_tune_batch",
+    "lbm_step_batch", "lbm_batch_plan", "lbm_batch_tiles", "lbm_pin_batch_plan", "lbm_tune_batch",
     "lbm_observe", "lbm_observe_enqueue", "lbm_observe_collect",
     "lbm_get_populations", "lbm_get_derived", "lbm_launch_count",
     "lbm_destroy", "lbm_last_error", "lbm_reduce_observables_noalloc", "lbm_probe_bounded_wait",
@@ -104,6 +104,9 @@ def load() -> ctypes.CDLL:
             L.lbm_step_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_int64]
             L.lbm_batch_plan.argtypes = [ctypes.POINTER(vp), ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_int32)]
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            L.lbm_batch_tiles.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, i32p, i32p]
+            L.lbm_pin_batch_plan.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, i32p, i32p]
             L.lbm_tune_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_int64)]
             L.lbm_observe.argtypes = [vp, ctypes.POINTER(LbmObs), dp]
@@ -210,12 +213,30 @@ def lbm_step_batch(sims, nsteps: int):
 
 
 def lbm_batch_plan(sims) -> list[int]:
-    """Strip length (chunks of 8 rows) lbm_step_batch uses for each sim; 0
-    for sims stepped by the tile kernel."""
+    """Strip length (in chunks of the tile shape's rows) lbm_step_batch uses
+    for each sim; 0 for sims stepped by the tile kernel."""
     arr, n = _handles(sims)
     out = (ctypes.c_int32 * n)()
     _check(load().lbm_batch_plan(arr, n, out), "lbm_batch_plan")
     return list(out)
+
+
+def lbm_batch_tiles(sims) -> list[tuple[int, int]]:
+    """(column width, chunk rows) of the streaming tile shape each sim is
+    stepped in; (0, 0) for sims stepped by the tile kernel."""
+    arr, n = _handles(sims)
+    w, h = (ctypes.c_int32 * n)(), (ctypes.c_int32 * n)()
+    _check(load().lbm_batch_tiles(arr, n, w, h), "lbm_batch_tiles")
+    return list(zip(list(w), list(h)))
+
+
+def lbm_pin_batch_plan(sims, tile_w, strip_chunks):
+    """Sets the batch's plan: tile width (32 or 64) and strip length of every
+    streaming sim (entries of the others are ignored)."""
+    arr, n = _handles(sims)
+    w = (ctypes.c_int32 * n)(*[int(x) for x in tile_w])
+    c = (ctypes.c_int32 * n)(*[int(x) for x in strip_chunks])
+    _check(load().lbm_pin_batch_plan(arr, n, w, c), "lbm_pin_batch_plan")
 
 
 def lbm_tune_batch(sims, trial_steps: int) -> int:

@@ -73,6 +73,7 @@ class LbmEngine:
         self.lbm = lbm
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.tiles: set[tuple[int, int]] = set()   # streaming tile shapes used
 
     def workspace_bytes(self, params: dict) -> int:
         return self.lbm.lbm_workspace_bytes(params)
@@ -84,7 +85,9 @@ class LbmEngine:
 
     def step(self, sims: list, n: int) -> None:
         for i in range(0, len(sims), MAX_BATCH):
-            self.lbm.lbm_step_batch(sims[i:i + MAX_BATCH], n)
+            batch = sims[i:i + MAX_BATCH]
+            self.lbm.lbm_step_batch(batch, n)
+            self.tiles.update(t for t in self.lbm.lbm_batch_tiles(batch) if t[0])
 
     def observe_enqueue(self, sims: list) -> None:
         for i in range(0, len(sims), MAX_BATCH):

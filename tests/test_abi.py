@@ -90,8 +90,9 @@ def test_batch_calls_reject_empty_batches_on_the_host():
     """Argument checks of the batch entry points run before any CUDA call."""
     from paper_2408_00146_gb300 import lbm
     for call in (lambda: lbm.lbm_step_batch([], 1), lambda: lbm.lbm_tune_batch([], 1),
-                 lambda: lbm.lbm_batch_plan([]), lambda: lbm.lbm_observe_enqueue([]),
-                 lambda: lbm.lbm_observe_collect([])):
+                 lambda: lbm.lbm_batch_plan([]), lambda: lbm.lbm_batch_tiles([]),
+                 lambda: lbm.lbm_pin_batch_plan([], [], []),
+                 lambda: lbm.lbm_observe_enqueue([]), lambda: lbm.lbm_observe_collect([])):
         with pytest.raises(lbm.LbmError) as ei:
             call()
         assert ei.value.status == lbm.LBM_EINVAL

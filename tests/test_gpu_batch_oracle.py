@@ -59,7 +59,10 @@ def _rows(p):
     return slice(1, p["ny"] - 1) if p["walls"] else slice(None)
 
 
-def test_uneven_batch_matches_oracle(lbm, orc):
+@pytest.mark.parametrize("tile_w", [None, 64])
+def test_uneven_batch_matches_oracle(lbm, orc, tile_w):
+    """The model's plan (32 x 8 tiles), and the 64 x 4 tile shape pinned for
+    the FP32 members."""
     import torch
     st = torch.cuda.Stream()
     fields = [si.parity_fields(p, seed=60 + i) for i, p in enumerate(MIX)]
@@ -69,6 +72,12 @@ def test_uneven_batch_matches_oracle(lbm, orc):
     plan = lbm.lbm_batch_plan(sims)
     assert plan[2] == 0 and plan[5] == 0                      # tile-kernel members
     assert all(plan[i] >= 4 for i in (0, 1, 3, 4))            # streaming members
+    if tile_w:
+        # FP32 members in the wide shape (16-bit storage has 32 x 8 only)
+        widths = [tile_w if p["precision"] == 0 else 32 for p in MIX]
+        lbm.lbm_pin_batch_plan(sims, widths, [5] * len(MIX))
+        assert all(lbm.lbm_batch_tiles(sims)[i] == (64, 4) for i in (0, 1))
+        assert all(lbm.lbm_batch_tiles(sims)[i] == (32, 8) for i in (3, 4))
     lbm.lbm_step_batch(sims, STEPS)
     for i, (p, f, sim) in enumerate(zip(MIX, fields, sims)):
         o = orc.Oracle(p)

@@ -1,7 +1,9 @@
 """Strip plans of the batched streaming launch: the plan lbm_step_batch uses
-(lbm_batch_plan) and its measured choice (lbm_tune_batch).  A step's result
-does not depend on the plan, so a tuned batch must hold exactly the
-populations of a batch stepped the same number of times without tuning."""
+(lbm_batch_plan, lbm_batch_tiles), its measured choice (lbm_tune_batch) and a
+plan set by the caller (lbm_pin_batch_plan).  A step's result does not depend
+on the plan -- tile shape and strip length -- so a tuned batch must hold
+exactly the populations of a batch stepped the same number of times without
+tuning, and the two compiled tile shapes must give identical steps."""
 import numpy as np
 import pytest
 
@@ -113,3 +115,56 @@ def test_graph_replayed_batch_equals_single_steps(lbm):
     for x, y in zip(a, b):
         assert np.array_equal(x.populations(), y.populations())
         assert x.observe()["t"] == y.observe()["t"]
+
+
+def test_tile_shapes_give_identical_steps(lbm):
+    """The 32 x 8 and 64 x 4 tile shapes (the second for FP32 storage only),
+    pinned on the same lattices (partial last columns of 16 and 32 nodes,
+    beside 16-bit streaming and tile-kernel lattices), step bit for bit
+    alike."""
+    import torch
+    ps = _mix()
+    st = torch.cuda.Stream()
+    a, b = _sims(lbm, ps, st), _sims(lbm, ps, st)
+    streaming = [c > 0 for c in lbm.lbm_batch_plan(a)]
+    fp32 = [p.get("precision", 0) == 0 for p in ps]
+    wide = [64 if f else 32 for f in fp32]
+    # plans are kept per list of lattice sizes: pin, step, then pin the other
+    lbm.lbm_pin_batch_plan(a, [32] * len(ps), [6] * len(ps))
+    assert lbm.lbm_batch_tiles(a) == [(32, 8) if s else (0, 0) for s in streaming]
+    lbm.lbm_step_batch(a, 70)        # one captured 64-step graph and single steps
+    lbm.lbm_pin_batch_plan(b, wide, [9] * len(ps))
+    assert lbm.lbm_batch_tiles(b) == [((64, 4) if f else (32, 8)) if s else (0, 0)
+                                      for s, f in zip(streaming, fp32)]
+    assert [c for c, s in zip(lbm.lbm_batch_plan(b), streaming) if s] == [9] * sum(streaming)
+    lbm.lbm_step_batch(b, 70)
+    for x, y in zip(a, b):
+        assert np.array_equal(x.populations(), y.populations())
+
+
+def test_tuned_plan_names_its_tile_shape(lbm):
+    import torch
+    ps = _mix()
+    sims = _sims(lbm, ps, torch.cuda.Stream())
+    lbm.lbm_tune_batch(sims, 1)
+    tiles = lbm.lbm_batch_tiles(sims)
+    plan = lbm.lbm_batch_plan(sims)
+    for (w, h), c in zip(tiles, plan):
+        assert (w, h) in ((32, 8), (64, 4)) if c > 0 else (w, h) == (0, 0)
+    # one shape per streaming launch; the 16-bit launches in 32 x 8
+    assert len({tiles[i] for i in range(3)}) == 1
+    assert tiles[5] == tiles[6] == (32, 8)
+
+
+def test_pin_rejects_bad_plans(lbm):
+    import torch
+    sims = _sims(lbm, _mix()[:3], torch.cuda.Stream())
+    for w, c in (([48] * 3, [8] * 3), ([32] * 3, [0] * 3), ([32, 64, 32], [8] * 3)):
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_pin_batch_plan(sims, w, c)
+        assert ei.value.status == lbm.LBM_EINVAL
+    # 64 x 4 has no 16-bit kernels
+    s16 = _sims(lbm, _mix()[5:6], torch.cuda.Stream())
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_pin_batch_plan(s16, [64], [8])
+    assert ei.value.status == lbm.LBM_EINVAL
