@@ -40,7 +40,8 @@ BYTES_PER_NODE_STEP = {"fp32": 288, "fp16": 176, "bf16": 176}
 BYTES_PER_NODE_BUFFER = {"fp32": 144, "fp16": 88, "bf16": 88}
 PRECISION_CODE = {"fp32": 0, "fp16": 1, "bf16": 2}
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-KERNEL_SRC = os.path.join(ROOT, "paper_2408_00146_gb300", "csrc", "lbm_stream.cu")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2408_00146_gb300", "csrc", f)
+              for f in ("lbm_stream.cu", "lbm_stream_body.cuh", "lbm_device.cuh")]
 
 
 def workload(name: str) -> list[dict]:
@@ -75,8 +76,12 @@ def measured_peaks() -> dict:
 
 
 def kernel_hash() -> str:
-    with open(KERNEL_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """Hash of the streaming kernels' sources (dispatch, body, device helpers)."""
+    h = hashlib.sha256()
+    for path in KERNEL_SRC:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def streams(p: dict, precision: str) -> bool:
