@@ -87,11 +87,11 @@ def kernel_hash() -> str:
 def streams(p: dict, precision: str) -> bool:
     """Whether the library steps this lattice with a y-streaming kernel:
     nx >= 32 and a multiple of 4 (FP32) or 8 (16-bit storage), at least 16 fluid rows,
-    walls or (FP32) a periodic y axis of whole 8-row chunks."""
+    walls or a periodic y axis of whole 8-row chunks."""
     nfy = p["ny"] - 2 if p["walls"] else p["ny"]
     if p["nx"] % (4 if precision == "fp32" else 8) or p["nx"] < 32 or nfy < 16:
         return False
-    return bool(p["walls"]) or (precision == "fp32" and nfy % 8 == 0)
+    return bool(p["walls"]) or nfy % 8 == 0
 
 
 def step_kernel_name(mode: str, precision: str, params=None) -> str:

@@ -638,6 +638,7 @@ static void stream16_entry(Stream16Args& a, int i, const lbm_sim* s, int from, i
     a.dev[i] = s->dev;
     a.dst[i] = s->pop[from ^ 1];
     a.mdst[i] = s->mom[from ^ 1];
+    a.msrc[i] = s->mom[from];
     a.err[i] = s->err;
     a.strip_chunks[i] = L;
     a.first[i + 1] = a.first[i] + stream_blocks(s->dev, L, sh);

@@ -125,6 +125,7 @@ struct Stream16Args {
     LbmDev dev[kMaxBatch16];
     void* dst[kMaxBatch16];     // deviations of the destination buffer
     void* mdst[kMaxBatch16];    // rest-state moments of the destination buffer
+    const void* msrc[kMaxBatch16];  // and of the source buffer (periodic y: wrapped rows)
     int* err[kMaxBatch16];
     int strip_chunks[kMaxBatch16];
     int first[kMaxBatch16 + 1];
@@ -135,8 +136,8 @@ static_assert(sizeof(StreamBatchArgs) <= 32764 && sizeof(Stream16Args) <= 32764,
 cudaError_t prepare_stream();
 // Whether a lattice of this storage precision can be stepped by the
 // streaming kernels: nx >= 32 and a multiple of 4 (FP32) or 8 (16-bit:
-// 16-byte TMA rows), at least 16 fluid rows, and walls or (FP32 only) a
-// periodic y axis of whole 8-row chunks.  The same lattices for every shape.
+// 16-byte TMA rows), at least 16 fluid rows, and walls or a periodic y axis
+// of whole 8-row chunks.  The same lattices for every shape.
 bool stream_eligible(const LbmDev& d, int precision);
 // Whether the tile shape has kernels for this storage precision (64 x 4:
 // FP32 only).

@@ -71,9 +71,8 @@ bool stream_eligible(const LbmDev& d, int precision)
     const int align = precision == LBM_FP32 ? 4 : 8;
     if (d.nx % align != 0 || d.nx < 32 || d.nfy < 16) return false;
     if (d.walls) return true;
-    // periodic y: whole chunks of every shape, and (16-bit) no wrap of the
-    // rest-state rows
-    return precision == LBM_FP32 && d.nfy % 8 == 0;
+    // periodic y: whole chunks of every shape
+    return d.nfy % 8 == 0;
 }
 
 int stream_columns(const LbmDev& d, int shape)

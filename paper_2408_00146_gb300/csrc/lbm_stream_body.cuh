@@ -759,6 +759,7 @@ struct Stage16 {
     const CUtensorMap* tmap;
     const CUtensorMap* tside;
     const CUtensorMap* tmom;
+    const float4* msrc;   // rest-state moments of the source buffer (global)
     static constexpr uint32_t bytes =
         (36u * TY * TX + 2u * 36u * TY * 8u) * 2u + kMomGroups * (TY + 2) * 8u * 16u;
     __device__ __forceinline__ void issue(int k, int st, uint32_t bar) const
@@ -817,6 +818,32 @@ struct Stage16 {
         const int o = ex > 0 ? m.west : (ex < 0 ? m.east : m.own);
         return *reinterpret_cast<const float4*>(base + o - ey * kMomRow);
     }
+    // Sources beyond the lattice's first or last row: next to a wall the
+    // population bounced back at the node itself (bounce_lo: the row above the
+    // bottom wall, bounce_hi: the row below the top wall); with periodic y the
+    // sources of row 0 lie in row ny - 1 and those of row ny - 1 in row 0,
+    // outside the stage's rows, and are read from the source buffer (wrap_lo,
+    // wrap_hi: those rows, else null; xg: the node's column).
+    struct Edge {
+        bool bounce_lo = false, bounce_hi = false;
+        const float4* wrap_lo = nullptr;
+        const float4* wrap_hi = nullptr;
+        int xg = 0, nx = 1;
+    };
+    __device__ __forceinline__ Edge edge_of(int phys, int c) const
+    {
+        Edge e;
+        if (d.walls) {
+            e.bounce_lo = phys == 1;
+            e.bounce_hi = phys == d.ny - 2;
+        } else {
+            if (phys == 0) e.wrap_lo = msrc + (size_t)(d.ny - 1) * d.nx;
+            if (phys == d.ny - 1) e.wrap_hi = msrc;
+        }
+        e.xg = sp.x0 + c;
+        e.nx = d.nx;
+        return e;
+    }
     // The differences t_a = f_a - k_a r of a node's populations, r its own rest
     // value: f_a = k_a m(src_a) + dev_a with src_a the node the population came
     // from (itself where it bounced off a wall), so t_a = k_a (m(src_a) - r) +
@@ -825,11 +852,11 @@ struct Stage16 {
     // packed pairs, and the sums accumulated in the order a = 0..8, which every
     // evaluation of a node's fields shares.  rest(m4, p): the rest values of
     // pair p from a float4; dev(p, a): the pair's two deviations of direction
-    // a; WALL: the row may be next to a wall (bot, top).
-    template <int NPAIR, bool WALL, class Dev, class Rest, class Acc>
-    __device__ __forceinline__ static void diffs16(const char* base, const MomAddr& ma, bool bot,
-                                                   bool top, const Dev& dev, float4 m0,
-                                                   const Rest& rest, const Acc& acc)
+    // a; EDGE: the row may be the lattice's first or last (edge).
+    template <int NPAIR, bool EDGE, class Dev, class Rest, class Acc>
+    __device__ __forceinline__ static void diffs16(const char* base, const MomAddr& ma, const Edge& edge,
+                                                   const Dev& dev, float4 m0, const Rest& rest,
+                                                   const Acc& acc)
     {
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
@@ -845,26 +872,32 @@ struct Stage16 {
             case 8: m4 = mom_src<1, -1>(base, ma); break;
             default: break;
             }
-            if (WALL) {
-                const int ey = ey_dir(a);
-                if ((ey > 0 && bot) || (ey < 0 && top)) m4 = m0;
+            if (EDGE) {
+                const int ey = ey_dir(a), ex = ex_dir(a);
+                if ((ey > 0 && edge.bounce_lo) || (ey < 0 && edge.bounce_hi)) m4 = m0;
+                const float4* wrow = ey > 0 ? edge.wrap_lo : (ey < 0 ? edge.wrap_hi : nullptr);
+                if (wrow) {
+                    int x = edge.xg - ex;
+                    x = x < 0 ? x + edge.nx : (x >= edge.nx ? x - edge.nx : x);
+                    m4 = wrow[x];
+                }
             }
 #pragma unroll
             for (int p = 0; p < NPAIR; ++p)
                 acc(p, a, fma2(f2(k_of_dir(a)), sub2(rest(m4, p), rest(m0, p)), dev(p, a)));
         }
     }
-    template <bool WALL, class Dev>
-    __device__ __forceinline__ Mom rebuild_moments(const char* base, const MomAddr& ma, bool bot,
-                                                   bool top, const Dev& dev) const
+    template <bool EDGE, class Dev>
+    __device__ __forceinline__ Mom rebuild_moments(const char* base, const MomAddr& ma, const Edge& edge,
+                                                   const Dev& dev) const
     {
         const float4 m0 = *reinterpret_cast<const float4*>(base + ma.own);
         float2 dd[2], jx[2], jy[2];
 #pragma unroll
         for (int p = 0; p < 2; ++p) dd[p] = jx[p] = jy[p] = f2(0.0f);
         float gnd = 0.0f, gxy = 0.0f;
-        diffs16<2, WALL>(
-            base, ma, bot, top,
+        diffs16<2, EDGE>(
+            base, ma, edge,
             [&](int p, int a) { return make_float2(s2f<T16>(dev(18 * p + a)), s2f<T16>(dev(18 * p + 9 + a))); },
             m0, [](const float4& v, int p) { return p == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w); },
             [&](int p, int a, float2 t) {
@@ -895,10 +928,10 @@ struct Stage16 {
         const auto dev = [&](int i) { return p[i * TY * TX]; };
         const MomAddr ma = mom_addr(tx, rb);
         const char* base = mom_base(st);
-        // a warp is one row: the wall test is uniform across it
-        const bool bot = d.walls && phys == 1, top = d.walls && phys == d.ny - 2;
-        if (bot || top) return rebuild_moments<true>(base, ma, bot, top, dev);
-        return rebuild_moments<false>(base, ma, false, false, dev);
+        // a warp is one row: the edge test is uniform across it
+        const bool edge = d.walls ? (phys == 1 || phys == d.ny - 2) : (phys == 0 || phys == d.ny - 1);
+        if (edge) return rebuild_moments<true>(base, ma, edge_of(phys, tx), dev);
+        return rebuild_moments<false>(base, ma, Edge{}, dev);
     }
     // Side items: 0, 1: phi at the outer columns -2, w + 1; 2..5: the inner
     // columns -1, w, set pair (f, g) or (h, q).  Every item takes the same
@@ -918,10 +951,9 @@ struct Stage16 {
         const MomAddr ma = mom_addr(c, r);
         const char* base = mom_base(st);
         const float4 m0 = *reinterpret_cast<const float4*>(base + ma.own);
-        const bool bot = d.walls && phys == 1, top = d.walls && phys == d.ny - 2;
         float2 dd = f2(0.0f);
         diffs16<1, true>(
-            base, ma, bot, top,
+            base, ma, edge_of(phys, c),
             [&](int, int a) { return make_float2(s2f<T16>(p[a * P]), s2f<T16>(p[(9 + a) * P])); }, m0,
             [f](const float4& v, int) { return f ? make_float2(v.z, v.w) : make_float2(v.x, v.y); },
             [&](int, int, float2 t) { dd = add2(dd, t); });
@@ -962,7 +994,8 @@ __global__ void __launch_bounds__(NT, BPS) stream16_kernel(const __grid_constant
     const LbmDev& d = args.dev[s];
     const Strip sp = strip_of(d, args.strip_chunks[s], blockIdx.x - args.first[s]);
     if (sp.c0 >= sp.c1) return;
-    Stage16<T16, S, SLOTS> stg{sm, d, sp, &args.tmap[s], &args.tside[s], &args.tmom[s]};
+    Stage16<T16, S, SLOTS> stg{sm, d, sp, &args.tmap[s], &args.tside[s], &args.tmom[s],
+                               static_cast<const float4*>(args.msrc[s])};
     walk<S, SLOTS>(d, sp, stg, sm.win, sm.bar, args.err[s],
                    Out16<T16>{static_cast<T16*>(args.dst[s]), static_cast<float4*>(args.mdst[s]),
                               d.nx * d.ny});

@@ -1,8 +1,9 @@
 """One lbm_step_batch over an uneven mix of simulations, every member checked
 against the FP64 oracle (not against itself): lattices of different sizes
-(partial last columns, a partial last chunk, a periodic lattice), both wall
-modes, FP32 with binary16 and bfloat16 storage, streaming and tile kernels,
-and different Gibbs elasticity, quadratic sensitivity and Marangoni number.
+(partial last columns, a partial last chunk, periodic lattices at FP32 and
+binary16 storage), both wall modes, FP32 with binary16 and bfloat16 storage,
+streaming and tile kernels, and different Gibbs elasticity, quadratic
+sensitivity and Marangoni number.
 
 Tolerances: FP32 members as the FP32 parity tests (fields within 1e-4 of each
 field's magnitude, velocities of U_o; centroid within 1e-3 lattice units;
@@ -52,6 +53,8 @@ MIX = [
     _member(64, 80, 1, 2, 0.25, 1e-3, 15.0, 8.0),
     # binary16, tile kernel (nx not a multiple of 8)
     _member(36, 64, 1, 1, 0.1, 4e-3, 45.0, 6.0),
+    # binary16, streaming, periodic y (rest-moment rows wrapped)
+    _member(48, 40, 0, 1, 0.1, 0.0, 12.0, 6.0),
 ]
 
 
@@ -71,13 +74,13 @@ def test_uneven_batch_matches_oracle(lbm, orc, tile_w):
         s.init(f)
     plan = lbm.lbm_batch_plan(sims)
     assert plan[2] == 0 and plan[5] == 0                      # tile-kernel members
-    assert all(plan[i] >= 4 for i in (0, 1, 3, 4))            # streaming members
+    assert all(plan[i] >= 4 for i in (0, 1, 3, 4, 6))         # streaming members
     if tile_w:
         # FP32 members in the wide shape (16-bit storage has 32 x 8 only)
         widths = [tile_w if p["precision"] == 0 else 32 for p in MIX]
         lbm.lbm_pin_batch_plan(sims, widths, [5] * len(MIX))
         assert all(lbm.lbm_batch_tiles(sims)[i] == (64, 4) for i in (0, 1))
-        assert all(lbm.lbm_batch_tiles(sims)[i] == (32, 8) for i in (3, 4))
+        assert all(lbm.lbm_batch_tiles(sims)[i] == (32, 8) for i in (3, 4, 6))
     lbm.lbm_step_batch(sims, STEPS)
     for i, (p, f, sim) in enumerate(zip(MIX, fields, sims)):
         o = orc.Oracle(p)

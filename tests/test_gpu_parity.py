@@ -107,12 +107,12 @@ def test_channel_64x128_2000_steps(lbm, orc, noise):
 
 def _streams(nx, ny, walls, precision=0):
     """Whether the streaming kernels take the lattice: nx >= 32 and a multiple
-    of 4 (FP32) or 8 (16-bit), at least 16 fluid rows, walls or (FP32) a
-    periodic y of whole 8-row chunks."""
+    of 4 (FP32) or 8 (16-bit), at least 16 fluid rows, walls or a periodic y
+    of whole 8-row chunks."""
     nfy = ny - 2 if walls else ny
     if nx % (4 if precision == 0 else 8) or nx < 32 or nfy < 16:
         return False
-    return bool(walls) or (precision == 0 and nfy % 8 == 0)
+    return bool(walls) or nfy % 8 == 0
 
 
 @pytest.mark.parametrize("nx,ny,walls", [(45, 37, 1), (37, 29, 0), (4, 5, 1), (4, 4, 0),

@@ -133,8 +133,9 @@ def test_channel_64x128_2000_steps(lbm, orc, prec, noise):
 @pytest.mark.parametrize("nx,ny,walls", [(45, 37, 1), (37, 29, 0), (4, 5, 1), (4, 4, 0),
                                          (33, 9, 1), (70, 19, 0),
                                          # streaming: partial last column and chunk, an
-                                         # 8-wide last column; periodic y (tile kernel)
-                                         (80, 63, 1), (40, 21, 1), (40, 24, 0)])
+                                         # 8-wide last column; periodic y (rest-moment
+                                         # rows wrapped), also with a partial column
+                                         (80, 63, 1), (40, 21, 1), (40, 24, 0), (80, 32, 0)])
 def test_ragged_and_minimal_lattices(lbm, orc, prec, nx, ny, walls):
     """Partial tiles (or a partial last column and chunk of the streaming
     kernel), the smallest lattices, both boundary modes, 30 steps.
@@ -150,7 +151,7 @@ def test_ragged_and_minimal_lattices(lbm, orc, prec, nx, ny, walls):
     sim = lbm.Sim(p)
     sim.init(f)
     nfy = ny - 2 if walls else ny
-    streams = nx % 8 == 0 and nx >= 32 and nfy >= 16 and bool(walls)
+    streams = nx % 8 == 0 and nx >= 32 and nfy >= 16 and (bool(walls) or nfy % 8 == 0)
     assert (lbm.lbm_batch_plan([sim])[0] > 0) == streams
     o = orc.Oracle(p)
     o.init_fields(f)
