@@ -610,7 +610,8 @@ struct Smem16 {
 //   own_moments(st, rb, tx, phys): the 14 moments of chunk row rb, column tx;
 //   side_item(st, item, r, phys, rw, W): side item 0 .. 5 of chunk row r (items
 //     0, 1: phi at columns -2, w + 1; 2..5: (phi, p*) or (T, psi) at columns -1
-//     and w).
+//     and w);
+//   side_slot(it, item, rr): the item and chunk row of the it-th side thread.
 template <int S, int SLOTS, class Stage, class Out>
 __device__ __forceinline__ void walk(const LbmDev& d, const Strip& sp, Stage& stg, Window<SLOTS>& W,
                                      uint64_t* bars, int* __restrict__ err, const Out& out)
@@ -648,9 +649,9 @@ __device__ __forceinline__ void walk(const LbmDev& d, const Strip& sp, Stage& st
                 put_fields(d, W, r, phys, tx, mc.f.s(), mc.g.s(), mc.h.s(), mc.q.s(), true);
             }
             if (tid >= NT - kSideItems) {
-                const int it = tid - (NT - kSideItems);
-                const int rr = it % TY;
-                stg.side_item(st, it / TY, rr, phys_row(d, Y + rr), Y + rr, W);
+                int item, rr;
+                Stage::side_slot(tid - (NT - kSideItems), item, rr);
+                stg.side_item(st, item, rr, phys_row(d, Y + rr), Y + rr, W);
             }
         }
         if (__syncthreads_or(!ok)) {
@@ -718,6 +719,12 @@ struct Stage32 {
     {
         const float* p = &sm.pop[st][0][rb][tx];
         return moments_of([&](int a) { return p[a * TY * TX]; });
+    }
+    // item by item, all rows of an item on consecutive threads
+    __device__ __forceinline__ static void side_slot(int it, int& item, int& rr)
+    {
+        item = it / TY;
+        rr = it % TY;
     }
     // items 0, 1: phi of the outer columns -2, w + 1; items 2..5: the inner
     // columns -1, w: (phi, p*) or (T, psi)
@@ -932,6 +939,24 @@ struct Stage16 {
         const bool edge = d.walls ? (phys == 1 || phys == d.ny - 2) : (phys == 0 || phys == d.ny - 1);
         if (edge) return rebuild_moments<true>(base, ma, edge_of(phys, tx), dev);
         return rebuild_moments<false>(base, ma, Edge{}, dev);
+    }
+    // The first 2 TY side threads take the second set pair (h, q) of the
+    // inner columns, two columns per row; the other 4 TY the first pair of all
+    // four side columns, four columns per row.  The threads of one warp then
+    // read one set pair's planes (no two addresses in one shared-memory bank
+    // within a 16-bit load), and each quarter warp the rest moments of four
+    // columns (two rows per bank instead of eight).
+    __device__ __forceinline__ static void side_slot(int it, int& item, int& rr)
+    {
+        if (it < 2 * TY) {
+            rr = it >> 1;
+            item = (it & 1) ? 5 : 3;     // inner column w or -1, pair (h, q)
+            return;
+        }
+        const int a = it - 2 * TY;
+        rr = a >> 2;
+        const int col = a & 3;           // columns -2, -1, w, w + 1
+        item = col == 0 ? 0 : (col == 1 ? 2 : (col == 2 ? 4 : 1));
     }
     // Side items: 0, 1: phi at the outer columns -2, w + 1; 2..5: the inner
     // columns -1, w, set pair (f, g) or (h, q).  Every item takes the same
