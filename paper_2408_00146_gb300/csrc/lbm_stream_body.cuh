@@ -674,8 +674,8 @@ __device__ __forceinline__ void walk(const LbmDev& d, const Strip& sp, Stage& st
         normals_rows(W, Y - 1, tid);
         __syncthreads();
         if (ty < 2) {
-            // rows 6 and 7 of this chunk are updated in the next iteration;
-            // this one updates those of the previous chunk
+            // the chunk's top two rows (TY - 2, TY - 1) are updated in the
+            // next iteration; this one updates those of the previous chunk
             const Mom prev = W.carry[ty][tx];
             if (have) W.carry[ty][tx] = mc;
             mc = prev;
