@@ -168,3 +168,23 @@ def test_pin_rejects_bad_plans(lbm):
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_pin_batch_plan(s16, [64], [8])
     assert ei.value.status == lbm.LBM_EINVAL
+
+
+def test_tile_shapes_identical_at_full_size(lbm):
+    """The largest lattice of the benchmarks, 1024 x 4096 (FP32), steps bit for
+    bit alike in the 32 x 8 and 64 x 4 tile shapes."""
+    import torch
+    p = si.channel_1024x4096()
+    st = torch.cuda.Stream()
+    a, b = lbm.Sim(p, stream=st), lbm.Sim(p, stream=st)
+    f = si.parity_fields(p, seed=3)
+    a.init(f)
+    b.init(f)
+    lbm.lbm_pin_batch_plan([a], [32], [57])
+    lbm.lbm_step_batch([a], 3)
+    lbm.lbm_pin_batch_plan([b], [64], [64])
+    assert lbm.lbm_batch_tiles([b]) == [(64, 4)]
+    lbm.lbm_step_batch([b], 3)
+    assert np.array_equal(a.populations(), b.populations())
+    a.close()
+    b.close()
