@@ -559,6 +559,10 @@ def run_gpu(args) -> None:
             prec: sub_measure(lbm, torch, dev_index, [si.channel_1024x4096()], prec, "batched",
                               args.extra_steps, args.tune_steps, stream, barrier)
             for prec in ("fp32", "fp16", "bf16")}
+        # the small 64x128 channel is launch-bound: its 2000 steps as lbm_step
+        # issues them (64-step CUDA graphs)
+        extra["config1"] = sub_measure(lbm, torch, dev_index, [si.channel_64x128()], "fp32",
+                                       "plain", 2000, 0, stream, barrier)
 
     e2e = run_e2e(args, lbm, torch, stream, params) if not args.no_e2e else None
     plain_value = extra.get("mixed_precision", {}).get("plain_fp32_single", {}).get("value")
@@ -730,7 +734,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=500,
                     help="requests of the served workload (0: skip it)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--serve-max-steps", type=int, default=200000,
+    ap.add_argument("--serve-max-steps", type=int, default=300000,
                     help="step cap of the served run to terminal state")
     ap.add_argument("--serve-throughput-steps", type=int, default=4000,
                     help="step cap of the served run over the full lattice range (0: skip)")
