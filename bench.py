@@ -441,12 +441,33 @@ def tile_shapes(lbm, sims) -> list[str]:
     return sorted({f"{w}x{h}" for w, h in lbm.lbm_batch_tiles(sims) if w})
 
 
+# lbm_step_batch replays a graph for every 64 steps of a call and for a
+# remainder of at least this many steps; lbm_step only for the 64-step runs
+GRAPH_MIN_STEPS = 8
+
+
 def launch_mode(mode, steps, per_step, graph):
-    """How the timed steps were issued: graphs replay only for runs of 64
-    steps in one call."""
+    """How the timed steps were issued: "graph" when captured graphs
+    replayed them (all of them, or all but a remainder of fewer than
+    GRAPH_MIN_STEPS single launches)."""
     if mode == "batched":
-        return "batched" + (" graph" if not per_step and steps >= 64 else "")
+        return "batched" + (" graph" if not per_step and steps >= GRAPH_MIN_STEPS else "")
     return "plain" + (" graph" if graph and steps >= 64 else "")
+
+
+def warm_remainder(batch, steps: int) -> int:
+    """A batched call of `steps` steps replays its own graph for the
+    remainder of steps mod 64 (when at least GRAPH_MIN_STEPS): capture it
+    before the timed region, from the buffers the timed call starts from
+    (twice for an odd remainder, so that they return).  Returns the steps
+    run."""
+    rem = steps % 64
+    if rem < GRAPH_MIN_STEPS:
+        return 0
+    n = 2 if rem % 2 else 1
+    for _ in range(n):
+        batch.run("batched", rem)
+    return n * rem
 
 
 def sub_measure(lbm, torch, dev_index, params, precision, mode, steps, tune_steps, stream,
@@ -457,6 +478,7 @@ def sub_measure(lbm, torch, dev_index, params, precision, mode, steps, tune_step
     if mode == "batched":
         b.tune(tune_steps)
         b.run(mode, 64)                   # warm-up that captures the batch graph
+        warm_remainder(b, steps)
     else:
         b.run(mode, 64, graph=graph)
     with ClockSampler(dev_index) as clk:
@@ -506,11 +528,14 @@ def run_gpu(args) -> None:
     plan = lbm.lbm_batch_plan(batch.sims)
     tiles = tile_shapes(lbm, batch.sims)
     warmup_run = args.warmup
-    if args.mode == "batched" and not args.per_step_calls and args.steps >= 64:
+    batched_call = args.mode == "batched" and not args.per_step_calls
+    if batched_call and args.steps >= 64:
         # at least one 64-step run, so that the batch's graph is captured
         # before the timed region
         warmup_run = max(args.warmup, 64)
     batch.run(args.mode, warmup_run, args.per_step_calls, args.graph)
+    if batched_call:
+        warmup_run += warm_remainder(batch, args.steps)
     with ClockSampler(dev_index) as clk:
         ms, launches = batch.timed(args.mode, args.steps, barrier, args.per_step_calls, args.graph)
     clocks = clk.summary()

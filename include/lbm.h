@@ -193,11 +193,12 @@ lbm_status lbm_step(lbm_sim* sim, int64_t nsteps);
  * lbm_step, so the result of every simulation equals what lbm_step gives it
  * alone.  All sims must be initialised, distinct, and created on the same
  * device and stream; the launches are issued on that stream (asynchronous)
- * and counted by lbm_launch_count of sims[0].  Runs of 64 steps replay a
- * CUDA graph captured on first use and cached per host thread for that list
- * of sims, their current buffers and the strip plan (8 graphs; a destroyed
- * sim's graphs are never replayed).  Errors: LBM_EINVAL, LBM_ESTATE,
- * LBM_ECUDA. */
+ * and counted by lbm_launch_count of sims[0].  Every 64 steps of a call, and
+ * a remaining run of 8 to 63 steps, replay a CUDA graph of that many steps,
+ * captured on first use and cached per host thread for that list of sims,
+ * their current buffers, the strip plan and the step count (8 graphs; a
+ * destroyed sim's graphs are never replayed); a remainder under 8 steps is
+ * launched step by step.  Errors: LBM_EINVAL, LBM_ESTATE, LBM_ECUDA. */
 lbm_status lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t nsteps);
 
 /* Strip plan of a batch.  Sims eligible for the streaming kernels (see

@@ -188,3 +188,21 @@ def test_tile_shapes_identical_at_full_size(lbm):
     assert np.array_equal(a.populations(), b.populations())
     a.close()
     b.close()
+
+
+def test_short_graph_runs_equal_single_steps(lbm):
+    """Batched calls of 8 to 63 steps replay a graph of their own once it is
+    captured; odd and even lengths, replayed twice, equal single steps."""
+    import torch
+    ps = _mix()
+    st = torch.cuda.Stream()
+    a, b = _sims(lbm, ps, st), _sims(lbm, ps, st)
+    l0a, l0b = a[0].launches(), b[0].launches()
+    for n in (20, 20, 13, 13, 7):
+        lbm.lbm_step_batch(a, n)
+        for _ in range(n):
+            lbm.lbm_step_batch(b, 1)
+    assert a[0].launches() - l0a == b[0].launches() - l0b
+    for x, y in zip(a, b):
+        assert x.observe()["t"] == y.observe()["t"] == 73
+        assert np.array_equal(x.populations(), y.populations())
