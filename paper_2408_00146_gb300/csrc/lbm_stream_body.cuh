@@ -1026,10 +1026,12 @@ __global__ void __launch_bounds__(NT, BPS) stream16_kernel(const __grid_constant
                               d.nx * d.ny});
 }
 
-// Kernel configurations: stages (FP32: one, refilled once the chunk's
-// moments are taken; 16-bit: two), resident blocks per SM (kStreamBlocksPerSm).
+// Kernel configurations: one stage for either storage, refilled once the
+// chunk's moments are taken (a second 16-bit stage measured 2 % slower: the
+// kernel is issue-bound, and the stage's 35 KB come out of the L1 share);
+// resident blocks per SM (kStreamBlocksPerSm).
 constexpr int kS32 = 1, kSlots32 = kSlots, kBps32 = kStreamBlocksPerSm;
-constexpr int kS16 = 2, kSlots16 = kSlots, kBps16 = kStreamBlocksPerSm;
+constexpr int kS16 = 1, kSlots16 = kSlots, kBps16 = kStreamBlocksPerSm;
 constexpr int kSmem32 = (int)sizeof(Smem32<kS32, kSlots32>);
 template <typename T16>
 constexpr int smem16() { return (int)sizeof(Smem16<T16, kS16, kSlots16>); }
