@@ -222,8 +222,9 @@ struct lbm_sim {
     CUtensorMap tmap[2];   // FP32 tile kernels: populations, box {kTileX, kTileY, 36}
     bool ystream;    // steps use a streaming kernel (stream_eligible, descriptors valid)
     // streaming kernels, per tile shape (W x H = kStreamW x kStreamH): the
-    // chunk (box {W, H, 36} of populations or deviations), the side columns
-    // (box {4, H, 36} FP32, {8, H, 36} 16-bit), the rest-state moments
+    // chunk (box {W, H, 36} of populations, {W, H, 18} of 16-bit pair words),
+    // the side columns (box {4, H, 36} FP32, {8, H, 18} 16-bit), the rest-state
+    // moments
     // (16-bit: box {4, 8, H + 2})
     CUtensorMap smap[kStreamShapes][2];
     CUtensorMap sside[kStreamShapes][2];
@@ -247,7 +248,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 // [36][ny][nx] for the tile kernels (box {kTileX, kTileY, 36}); for each
 // streaming tile shape W x H the chunk box {W, H, 36} and the side box
 // {4, H, 36}; TMA needs 16-byte row strides, nx % 4 == 0.  16-bit storage:
-// the deviations [36][ny][nx] (boxes {W, H, 36} and {8, H, 36}; nx % 8 == 0)
+// the deviations as 32-bit words of set pairs [18][ny][nx] (boxes {W, H, 18}
+// and {8, H, 18}; nx % 8 == 0)
 // and the rest-state moments, the float4 array [ny][nx] viewed as
 // [ny][nx][4] floats (box {4, 8, H + 2}).  Without them every step takes the
 // tile kernels, which stage with plain loads.
@@ -262,9 +264,12 @@ bool encode_population_maps(lbm_sim* s)
         q != cudaDriverEntryPointSuccess || !fn)
         return false;
     EncodeTiledFn encode = reinterpret_cast<EncodeTiledFn>(fn);
-    const cuuint64_t esz = fp32 ? sizeof(float) : 2;
-    const CUtensorMapDataType dt = fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-    const cuuint64_t dims[3] = {(cuuint64_t)s->p.nx, (cuuint64_t)s->p.ny, 36};
+    // FP32: 36 planes of floats; 16-bit: 18 planes of 32-bit words, each the
+    // two values of a set pair (f, g) or (h, q)
+    const cuuint64_t esz = 4;
+    const cuuint32_t planes = fp32 ? 36 : 18;
+    const CUtensorMapDataType dt = fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+    const cuuint64_t dims[3] = {(cuuint64_t)s->p.nx, (cuuint64_t)s->p.ny, planes};
     const cuuint64_t strides[2] = {(cuuint64_t)s->p.nx * esz, (cuuint64_t)s->p.nx * s->p.ny * esz};
     const cuuint32_t estride[3] = {1, 1, 1};
     const cuuint64_t mdims[3] = {4, (cuuint64_t)s->p.nx, (cuuint64_t)s->p.ny};
@@ -283,8 +288,8 @@ bool encode_population_maps(lbm_sim* s)
         for (int sh = 0; sh < kStreamShapes; ++sh) {
             if (!stream_shape_available(sh, s->p.precision)) continue;
             const cuuint32_t H = (cuuint32_t)kStreamH[sh];
-            const cuuint32_t box[3] = {(cuuint32_t)kStreamW[sh], H, 36};
-            const cuuint32_t side_box[3] = {fp32 ? 4u : 8u, H, 36};
+            const cuuint32_t box[3] = {(cuuint32_t)kStreamW[sh], H, planes};
+            const cuuint32_t side_box[3] = {fp32 ? 4u : 8u, H, planes};
             if (!enc(&s->smap[sh][b], dt, s->pop[b], dims, strides, box)) return false;
             if (!enc(&s->sside[sh][b], dt, s->pop[b], dims, strides, side_box)) return false;
             if (fp32) continue;

@@ -214,6 +214,37 @@ template <> __device__ __forceinline__ __nv_bfloat16 f2s<__nv_bfloat16>(float v)
 {
     return __float2bfloat16_rn(v);
 }
+// Two values of a set pair in one 32-bit word (the first in the low half),
+// each rounded to nearest even as f2s rounds it, and back.
+template <typename S> __device__ __forceinline__ uint32_t f2s2(float a, float b);
+template <> __device__ __forceinline__ uint32_t f2s2<__half>(float a, float b)
+{
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <> __device__ __forceinline__ uint32_t f2s2<__nv_bfloat16>(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <typename S> __device__ __forceinline__ float2 s2f2(uint32_t v);
+template <> __device__ __forceinline__ float2 s2f2<__half>(uint32_t v)
+{
+    return __half22float2(*reinterpret_cast<const __half2*>(&v));
+}
+template <> __device__ __forceinline__ float2 s2f2<__nv_bfloat16>(uint32_t v)
+{
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v));
+}
+
+// 16-bit storage layout: the sets are stored in pairs, (f, g) and (h, q),
+// the pair's two values of a population side by side in one 32-bit word,
+// [2 pairs][9 directions][ny][nx][2].  Element of population a of set s at
+// node o (N = nx ny nodes).
+__device__ __forceinline__ size_t dev_index(int s, int a, size_t N, size_t o)
+{
+    return (((size_t)(s >> 1) * 9 + a) * N + o) * 2 + (s & 1);
+}
 
 __device__ __forceinline__ constexpr float w_of_dir(int a)
 {

@@ -625,7 +625,8 @@ __global__ void init_equilibrium_kernel(LbmDev d, const float* __restrict__ fld,
 // m_s(x) = M_s(x)/36 of the populations x pushed at the last step (FP32, one
 // float4 (f, g, h, q) per node; M_s the set's zeroth moment), and per
 // population its deviation from the lattice-weighted rest state of the node
-// that pushed it (16-bit, [36][ny][nx]):
+// that pushed it (16-bit, the set pairs (f, g) and (h, q) side by side,
+// [2][9][ny][nx][2], dev_index):
 //     f_a(y) = k_a m(src_a(y)) + dev_a(y),   src_a(y) = y - e_a,
 // or y itself when y - e_a is a wall row (the population bounced back at y),
 // with the integer weights k_a = 36 w_a = 16, 4, 1: k_a m is exact in FP32 and
@@ -657,6 +658,8 @@ __device__ __forceinline__ float rebuild(const LbmDev& d, const float (*m)[kMH][
 // k_a m with m = M/36 (M: the set's post-collision zeroth moment); returns the
 // rest-state value to record for them, m plus the rounding errors of the nine
 // stored deviations over 36, so that they sum to their FP32 values.
+// dst_set: the set's first element (dev_index(set, 0, N, 0)); population a of
+// node o is element 2 (a N + o) from it.
 template <typename S, bool kEnergy>
 __device__ __forceinline__ float store_set_dev(S* __restrict__ dst_set, int N, const Nbr& nb,
                                                const float v[9], float M, int wall, float Tw)
@@ -685,30 +688,30 @@ __device__ __forceinline__ float store_set_dev(S* __restrict__ dst_set, int N, c
         lost += dv - s2f<S>(q[a]);
     }
     const int o0 = nb.o[0];
-    dst_set[o0] = q[0];
-    dst_set[N + nb.o[1]] = q[1];
-    dst_set[3 * N + nb.o[3]] = q[3];
+    dst_set[2 * o0] = q[0];
+    dst_set[2 * (N + nb.o[1])] = q[1];
+    dst_set[2 * (3 * N + nb.o[3])] = q[3];
     if (wall == 0) {
-        dst_set[2 * N + nb.o[2]] = q[2];
-        dst_set[4 * N + nb.o[4]] = q[4];
-        dst_set[5 * N + nb.o[5]] = q[5];
-        dst_set[6 * N + nb.o[6]] = q[6];
-        dst_set[7 * N + nb.o[7]] = q[7];
-        dst_set[8 * N + nb.o[8]] = q[8];
+        dst_set[2 * (2 * N + nb.o[2])] = q[2];
+        dst_set[2 * (4 * N + nb.o[4])] = q[4];
+        dst_set[2 * (5 * N + nb.o[5])] = q[5];
+        dst_set[2 * (6 * N + nb.o[6])] = q[6];
+        dst_set[2 * (7 * N + nb.o[7])] = q[7];
+        dst_set[2 * (8 * N + nb.o[8])] = q[8];
     } else if (wall < 0) {
-        dst_set[2 * N + nb.o[2]] = q[2];
-        dst_set[5 * N + nb.o[5]] = q[5];
-        dst_set[6 * N + nb.o[6]] = q[6];
-        dst_set[2 * N + o0] = q[4];
-        dst_set[5 * N + o0] = q[7];
-        dst_set[6 * N + o0] = q[8];
+        dst_set[2 * (2 * N + nb.o[2])] = q[2];
+        dst_set[2 * (5 * N + nb.o[5])] = q[5];
+        dst_set[2 * (6 * N + nb.o[6])] = q[6];
+        dst_set[2 * (2 * N + o0)] = q[4];
+        dst_set[2 * (5 * N + o0)] = q[7];
+        dst_set[2 * (6 * N + o0)] = q[8];
     } else {
-        dst_set[4 * N + nb.o[4]] = q[4];
-        dst_set[7 * N + nb.o[7]] = q[7];
-        dst_set[8 * N + nb.o[8]] = q[8];
-        dst_set[4 * N + o0] = q[2];
-        dst_set[7 * N + o0] = q[5];
-        dst_set[8 * N + o0] = q[6];
+        dst_set[2 * (4 * N + nb.o[4])] = q[4];
+        dst_set[2 * (7 * N + nb.o[7])] = q[7];
+        dst_set[2 * (8 * N + nb.o[8])] = q[8];
+        dst_set[2 * (4 * N + o0)] = q[2];
+        dst_set[2 * (7 * N + o0)] = q[5];
+        dst_set[2 * (8 * N + o0)] = q[6];
     }
     return fmaf(lost, kInv36, m);
 }
@@ -723,7 +726,7 @@ struct StoreDev {
     __device__ __forceinline__ float put(int set, int N, const Nbr& nb, const float v[9], float M,
                                          int wall, float Tw) const
     {
-        return store_set_dev<S, kEnergy>(dev + (size_t)set * 9 * N, N, nb, v, M, wall, Tw);
+        return store_set_dev<S, kEnergy>(dev + dev_index(set, 0, N, 0), N, nb, v, M, wall, Tw);
     }
     __device__ __forceinline__ void finish(int o, float Mf, float Mg, float Mh, float Mq) const
     {
@@ -791,13 +794,13 @@ __device__ __forceinline__ void step_tile_dev(const LbmDev& d, const S* __restri
         const int sx = wrap_x(d, gx);
         const int sy = src_row(d, gy, own_side);
         const int my = mrow(ty + 3, sy);
-        const S* p = dsrc + (sy * d.nx + sx);
+        const int o = sy * d.nx + sx;
 #pragma unroll
         for (int s = 0; s < 4; ++s)
 #pragma unroll
             for (int a = 0; a < 9; ++a)
                 s_pop[9 * s + a][ty][tx] =
-                    rebuild(d, s_m, s, a, tx + 3, my, sy, s2f<S>(__ldg(p + (9 * s + a) * N)));
+                    rebuild(d, s_m, s, a, tx + 3, my, sy, s2f<S>(__ldg(dsrc + dev_index(s, a, N, o))));
     }
 
     for (int i = tid; i < EW * EH; i += TX * TY) {
@@ -808,14 +811,14 @@ __device__ __forceinline__ void step_tile_dev(const LbmDev& d, const S* __restri
         const int sx = wrap_x(d, x0 + ex - 2);
         const int sy = src_row(d, d.y0 + fy0 + ey - 2, side);
         const int my = mrow(ey + 1, sy);
-        const S* p = dsrc + (sy * d.nx + sx);
+        const int o = sy * d.nx + sx;
         float sums[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         const int nsets = ring1 ? 4 : 1;
         for (int s = 0; s < nsets; ++s) {
             float v[9];
 #pragma unroll
             for (int a = 0; a < 9; ++a)
-                v[a] = rebuild(d, s_m, s, a, ex + 1, my, sy, s2f<S>(__ldg(p + (9 * s + a) * N)));
+                v[a] = rebuild(d, s_m, s, a, ex + 1, my, sy, s2f<S>(__ldg(dsrc + dev_index(s, a, N, o))));
             sums[s] = sum9(v);
         }
         halo_fields(d, sm, ex, ey, ring1, side, sums[0], sums[1], sums[2], sums[3]);
@@ -889,7 +892,7 @@ __global__ void split_planes_kernel(LbmDev d, const float* __restrict__ pl, int 
         float4 mv = mom[src_node(d, x, y, a)];
         const float dv = fmaf(-k_of_dir(a), comp(mv, s), pl[(size_t)k * N + o]);
         const S q = f2s<S>(dv);
-        dev[(size_t)(a0 + k) * N + o] = q;
+        dev[dev_index(s, a, N, o)] = q;
         comp(l, s) += dv - s2f<S>(q);
     }
     lost[o] = l;
@@ -929,7 +932,7 @@ __global__ void join_planes_kernel(LbmDev d, const S* __restrict__ dev,
         if (fluid) {
             const float4 mv = mom[src_node(d, x, y, a)];
             const float ms = s == 0 ? mv.x : (s == 1 ? mv.y : (s == 2 ? mv.z : mv.w));
-            v = fmaf(k_of_dir(a), ms, s2f<S>(dev[(size_t)(a0 + k) * N + o]));
+            v = fmaf(k_of_dir(a), ms, s2f<S>(dev[dev_index(s, a, N, o)]));
         }
         pl[(size_t)k * N + o] = v;
     }
@@ -959,7 +962,7 @@ __global__ void init_dev_kernel(LbmDev d, const float* __restrict__ fld, S* __re
             const float ms = fld[(size_t)kField[s] * N + src_node(d, x, y, a)] * kInv36;
             const float dv = fmaf(-k_of_dir(a), ms, out[a]);
             const S q = f2s<S>(dv);
-            dev[(size_t)(9 * s + a) * N + o] = q;
+            dev[dev_index(s, a, N, o)] = q;
             lost[s] += dv - s2f<S>(q);
         }
     }

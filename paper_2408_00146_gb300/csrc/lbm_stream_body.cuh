@@ -296,6 +296,7 @@ __device__ __forceinline__ bool into_wall(int a, int wall)
 
 // FP32 populations pushed to the neighbours.
 struct Out32 {
+    static constexpr bool kPairs = false;
     float* dst;
     int N;
     // a scalar scheme with zeroth moment 36 r + d from its deviations dev_a
@@ -338,13 +339,19 @@ struct Out32 {
 // weights k_a = 16, 4, 1, see lbm_kernels.cu), and at the node its rest value
 // m + (M - 36 m - sum of the nine stored deviations)/36, so that the nine
 // pushed populations rebuild (k_a m + stored deviation) to exactly M, whatever
-// the rounding of the deviations themselves.
+// the rounding of the deviations themselves.  The sets are stored in pairs,
+// (f, g) and (h, q), one 32-bit word per population and pair: the first set
+// of a pair to be computed (g, h: kPairs orders update_node's collisions
+// g, f, h, q) is held until the second, and each word is rounded, stored
+// and summed for the rest values in one step.
 template <typename S>
 struct Out16 {
-    S* dst;
+    static constexpr bool kPairs = true;
+    uint32_t* dst;
     float4* mdst;
     int N;
     mutable float M[4];
+    mutable float held[9], held_m, held_target;   // the pair's first set
     // scalar scheme, zeroth moment 36 r + d conserved: m = r + d/36 and the
     // residue 36 r + d - 36 m (exact) goes to the rest population
     __device__ __forceinline__ void scalar(int set, const Dest& D, const SetMom& ms,
@@ -372,22 +379,44 @@ struct Out16 {
     __device__ __forceinline__ void store(int set, const Dest& D, float m, float target,
                                           const float dev[9], bool dirichlet, float Tw) const
     {
-        S* p = dst + (size_t)set * 9 * N;
-        float stored = 0.0f;
+        float dv[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            float dv = dev[a];
-            const bool wl = into_wall(a, D.wall);
-            if (wl && dirichlet) {
-                const float out = fmaf(2.0f * k_of_dir(a), fmaf(Tw, kInv36, -m), -dv);
-                target += out - dv;
-                dv = out;
+            dv[a] = dev[a];
+            if (into_wall(a, D.wall) && dirichlet) {
+                const float out = fmaf(2.0f * k_of_dir(a), fmaf(Tw, kInv36, -m), -dv[a]);
+                target += out - dv[a];
+                dv[a] = out;
             }
-            const S q = f2s<S>(dv);
-            stored += s2f<S>(q);
-            p[(wl ? opp_dir(a) : a) * N + (wl ? D.o[0] : D.o[a])] = q;
         }
-        M[set] = fmaf(target - stored, kInv36, m);
+        if (set == 1 || set == 2) {   // first of its pair: hold
+#pragma unroll
+            for (int a = 0; a < 9; ++a) held[a] = dv[a];
+            held_m = m;
+            held_target = target;
+            return;
+        }
+        // set 0 completes (f, g), set 3 completes (h, q)
+        const int pr = set >> 1;
+        float lo[9], hi[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            lo[a] = pr == 0 ? dv[a] : held[a];
+            hi[a] = pr == 0 ? held[a] : dv[a];
+        }
+        uint32_t* p = dst + (size_t)pr * 9 * N;
+        float2 stored = f2(0.0f);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const bool wl = into_wall(a, D.wall);
+            const uint32_t w = f2s2<S>(lo[a], hi[a]);
+            stored = add2(stored, s2f2<S>(w));
+            p[(wl ? opp_dir(a) : a) * N + (wl ? D.o[0] : D.o[a])] = w;
+        }
+        const float m_lo = pr == 0 ? m : held_m, m_hi = pr == 0 ? held_m : m;
+        const float t_lo = pr == 0 ? target : held_target, t_hi = pr == 0 ? held_target : target;
+        M[2 * pr] = fmaf(t_lo - stored.x, kInv36, m_lo);
+        M[2 * pr + 1] = fmaf(t_hi - stored.y, kInv36, m_hi);
     }
     __device__ __forceinline__ void finish(const Dest& D) const
     {
@@ -440,7 +469,7 @@ __device__ __forceinline__ void update_node(const LbmDev& d, const Window<SLOTS>
     const Axis X = axis_of(ux), Y = axis_of(uy);
 
     // ---- f: conservative Allen-Cahn (App. B, Eqs. (26)-(27)) ------------------------------
-    {
+    const auto collide_f = [&]() {
         const float theta_m = d.mphi_4_over_W * phi * (1.0f - phi);   // M_phi theta
         const float c10 = m.f.jx - ux * phi, c01 = m.f.jy - uy * phi;
         const float A = c10 + d.omega_phi * (theta_m * n_x - c10);
@@ -456,9 +485,9 @@ __device__ __forceinline__ void update_node(const LbmDev& d, const Window<SLOTS>
         dev[7] = scalar_dev<7>(X, Y, phi, A, B);
         dev[8] = scalar_dev<8>(X, Y, phi, A, B);
         out.scalar(0, D, m.f, dev, false, 0.0f);
-    }
+    };
     // ---- h: energy (App. D, Eqs. (37)-(38)), rate from the local diffusivity ----------------
-    {
+    const auto collide_h = [&]() {
         const float alpha = d.alphaA + pc * d.dalpha;
         const float wT = __fdividef(1.0f, 3.0f * alpha + 0.5f);
         const float T = m.h.s();
@@ -475,9 +504,9 @@ __device__ __forceinline__ void update_node(const LbmDev& d, const Window<SLOTS>
         dev[7] = scalar_dev<7>(X, Y, T, A, B);
         dev[8] = scalar_dev<8>(X, Y, T, A, B);
         out.scalar(2, D, m.h, dev, true, D.wall < 0 ? d.T_H : d.T_C);
-    }
+    };
     // ---- q: surfactant (App. E, Eqs. (42)-(43)) -------------------------------------------
-    {
+    const auto collide_q = [&]() {
         const float psi = m.q.s();
         const float dG = (phi - 0.5f) * (d.g_s32 * phi * (1.0f - phi) + d.g_w);
         const float flux = -d.m_psi * psi * (1.0f - psi) * dG;   // times grad phi
@@ -496,9 +525,9 @@ __device__ __forceinline__ void update_node(const LbmDev& d, const Window<SLOTS>
         dev[8] = scalar_dev<8>(X, Y, psi, A, B);
         // walls: halfway bounce-back, or anti-bounce-back with psi_L / psi_R
         out.scalar(3, D, m.q, dev, d.psi_bc == 1, D.wall < 0 ? d.psi_L : d.psi_R);
-    }
+    };
     // ---- g: two-fluid pressure/velocity (App. C, Eqs. (31)-(34)) ----------------------------
-    {
+    const auto collide_g = [&]() {
         const float mu = d.muA + pc * d.dmu;
         const float wn = __fdividef(1.0f, 3.0f * mu * inv_rho + 0.5f);
         const float vp = p - rho * kCs2;                      // varphi = p - rho c_s^2
@@ -531,6 +560,19 @@ __device__ __forceinline__ void update_node(const LbmDev& d, const Window<SLOTS>
         central_to_pop(n00, n10, n01, 0.5f * (n2s + n2d), 0.5f * (n2s - n2d), n11, e21, e12, e22,
                        ux, uy, v);
         out.general(1, D, n00, v);
+    };
+    // 16-bit storage writes the sets in pairs (f, g), (h, q), each pair's
+    // second set completing it
+    if constexpr (Out::kPairs) {
+        collide_g();
+        collide_f();
+        collide_h();
+        collide_q();
+    } else {
+        collide_f();
+        collide_h();
+        collide_q();
+        collide_g();
     }
     out.finish(D);
 }
@@ -590,15 +632,16 @@ struct Smem32 {
     uint64_t bar[S];
 };
 
-// 16-bit storage: the chunk's deviations (box {TX, TY, 36}), eight columns
-// on each side (boxes {8, TY, 36}) and the rest-state moments of rows
+// 16-bit storage: the chunk's deviations as 32-bit words of set pairs, (f, g)
+// in planes 0 .. 8 and (h, q) in planes 9 .. 17 (box {TX, TY, 18}), eight
+// columns on each side (boxes {8, TY, 18}) and the rest-state moments of rows
 // -1 .. TY of the chunk in kMomGroups groups of eight columns (boxes
 // {4, 8, TY + 2} of the float4 array), group g covering local columns
 // 8 g - 8 .. 8 g - 1.
 template <typename T16, int S, int SLOTS>
 struct Smem16 {
-    T16 dev[S][36][TY][TX];
-    T16 side[S][2][36][TY][8];
+    uint32_t dev[S][18][TY][TX];
+    uint32_t side[S][2][18][TY][8];
     float4 mom[S][kMomGroups][TY + 2][8];
     Window<SLOTS> win;
     uint64_t bar[S];
@@ -768,7 +811,7 @@ struct Stage16 {
     const CUtensorMap* tmom;
     const float4* msrc;   // rest-state moments of the source buffer (global)
     static constexpr uint32_t bytes =
-        (36u * TY * TX + 2u * 36u * TY * 8u) * 2u + kMomGroups * (TY + 2) * 8u * 16u;
+        (18u * TY * TX + 2u * 18u * TY * 8u) * 4u + kMomGroups * (TY + 2) * 8u * 16u;
     __device__ __forceinline__ void issue(int k, int st, uint32_t bar) const
     {
         const int y = chunk_row(d, sp, k);
@@ -905,7 +948,7 @@ struct Stage16 {
         float gnd = 0.0f, gxy = 0.0f;
         diffs16<2, EDGE>(
             base, ma, edge,
-            [&](int p, int a) { return make_float2(s2f<T16>(dev(18 * p + a)), s2f<T16>(dev(18 * p + 9 + a))); },
+            [&](int p, int a) { return s2f2<T16>(dev(9 * p + a)); },
             m0, [](const float4& v, int p) { return p == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w); },
             [&](int p, int a, float2 t) {
                 const int ex = ex_dir(a), ey = ey_dir(a);
@@ -931,7 +974,7 @@ struct Stage16 {
     }
     __device__ __forceinline__ Mom own_moments(int st, int rb, int tx, int phys) const
     {
-        const T16* p = &sm.dev[st][0][rb][tx];
+        const uint32_t* p = &sm.dev[st][0][rb][tx];
         const auto dev = [&](int i) { return p[i * TY * TX]; };
         const MomAddr ma = mom_addr(tx, rb);
         const char* base = mom_base(st);
@@ -971,7 +1014,7 @@ struct Stage16 {
         const int f = outer ? 0 : (item - 2) % 2;
         const int c = outer ? (lr ? sp.w + 1 : -2) : (lr ? sp.w : -1);
         const int bc = lr ? c - sp.w : c + 8;
-        const T16* p = &sm.side[st][lr][18 * f][r][bc];
+        const uint32_t* p = &sm.side[st][lr][9 * f][r][bc];
         constexpr int P = TY * 8;
         const MomAddr ma = mom_addr(c, r);
         const char* base = mom_base(st);
@@ -979,7 +1022,7 @@ struct Stage16 {
         float2 dd = f2(0.0f);
         diffs16<1, true>(
             base, ma, edge_of(phys, c),
-            [&](int, int a) { return make_float2(s2f<T16>(p[a * P]), s2f<T16>(p[(9 + a) * P])); }, m0,
+            [&](int, int a) { return s2f2<T16>(p[a * P]); }, m0,
             [f](const float4& v, int) { return f ? make_float2(v.z, v.w) : make_float2(v.x, v.y); },
             [&](int, int, float2 t) { dd = add2(dd, t); });
         const float d1 = dd.x, d2 = dd.y;
@@ -1022,7 +1065,7 @@ __global__ void __launch_bounds__(NT, BPS) stream16_kernel(const __grid_constant
     Stage16<T16, S, SLOTS> stg{sm, d, sp, &args.tmap[s], &args.tside[s], &args.tmom[s],
                                static_cast<const float4*>(args.msrc[s])};
     walk<S, SLOTS>(d, sp, stg, sm.win, sm.bar, args.err[s],
-                   Out16<T16>{static_cast<T16*>(args.dst[s]), static_cast<float4*>(args.mdst[s]),
+                   Out16<T16>{static_cast<uint32_t*>(args.dst[s]), static_cast<float4*>(args.mdst[s]),
                               d.nx * d.ny});
 }
 
