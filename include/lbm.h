@@ -60,7 +60,9 @@ typedef enum {
  *     (16 B), and per population its deviation from k_a m of the node that
  *     pushed it (the source y - e_a, or the node itself for a population that
  *     bounced back), stored in IEEE binary16 or bfloat16 (72 B per node and
- *     buffer); k_a = 36 w_a = 16, 4, 1 are exact integer weights.  The rest
+ *     buffer; the sets in pairs, (f, g) and (h, q), the two deviations of a
+ *     population side by side in one 32-bit word); k_a = 36 w_a = 16, 4, 1
+ *     are exact integer weights.  The rest
  *     part carries the conserved scalars phi, T, psi in FP32; the rounding
  *     errors of the nine deviations a node pushes are folded into its m, so
  *     the populations it pushes sum to their FP32 values.  Populations at the
