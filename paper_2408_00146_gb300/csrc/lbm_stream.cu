@@ -34,10 +34,15 @@
 #include "lbm_internal.h"
 #include "lbm_device.cuh"
 
+// LBM_WALK_LAG: the 16-bit kernels walk their strips with one barrier per
+// chunk (walk_lag); the FP32 kernels keep two (walk), which measured 2.5 %
+// faster for them.
 namespace shape_32x8 {
 constexpr int TX = 32, TY = 8;
 #define LBM_STREAM_16BIT 1
+#define LBM_WALK_LAG 1
 #include "lbm_stream_body.cuh"
+#undef LBM_WALK_LAG
 #undef LBM_STREAM_16BIT
 }  // namespace shape_32x8
 
@@ -46,7 +51,9 @@ constexpr int TX = 32, TY = 8;
 namespace shape_64x4 {
 constexpr int TX = 64, TY = 4;
 #define LBM_STREAM_16BIT 0
+#define LBM_WALK_LAG 0
 #include "lbm_stream_body.cuh"
+#undef LBM_WALK_LAG
 #undef LBM_STREAM_16BIT
 }  // namespace shape_64x4
 

@@ -622,6 +622,36 @@ __device__ __forceinline__ int phys_row(const LbmDev& d, int r)
     return r < 0 ? r + d.ny : (r >= d.ny ? r - d.ny : r);
 }
 
+#if LBM_WALK_LAG
+// A node's moments parked in shared memory for one iteration, one float per
+// thread and component (conflict-free), two buffers by iteration parity.
+struct Park {
+    float v[2][18][NT];
+    __device__ __forceinline__ void put(int par, int tid, const Mom& m)
+    {
+        const float x[18] = {m.f.r, m.f.d, m.f.jx, m.f.jy, m.g.r, m.g.d, m.g.jx, m.g.jy, m.h.r,
+                             m.h.d, m.h.jx, m.h.jy, m.q.r, m.q.d, m.q.jx, m.q.jy, m.gnd, m.gxy};
+#pragma unroll
+        for (int i = 0; i < 18; ++i) v[par][i][tid] = x[i];
+    }
+    __device__ __forceinline__ Mom get(int par, int tid) const
+    {
+        float x[18];
+#pragma unroll
+        for (int i = 0; i < 18; ++i) x[i] = v[par][i][tid];
+        Mom m;
+        m.f = SetMom{x[0], x[1], x[2], x[3]};
+        m.g = SetMom{x[4], x[5], x[6], x[7]};
+        m.h = SetMom{x[8], x[9], x[10], x[11]};
+        m.q = SetMom{x[12], x[13], x[14], x[15]};
+        m.gnd = x[16];
+        m.gxy = x[17];
+        return m;
+    }
+};
+
+#endif
+
 // FP32 storage: the chunk (box {TX, TY, 36}) and four columns on each side
 // (boxes {4, TY, 36}) per stage.
 template <int S, int SLOTS>
@@ -644,6 +674,9 @@ struct Smem16 {
     uint32_t side[S][2][18][TY][8];
     float4 mom[S][kMomGroups][TY + 2][8];
     Window<SLOTS> win;
+#if LBM_WALK_LAG
+    Park park;
+#endif
     uint64_t bar[S];
 };
 
@@ -737,6 +770,94 @@ __device__ __forceinline__ void walk(const LbmDev& d, const Strip& sp, Stage& st
         if (SLOTS < 2 * TY + 7) __syncthreads();
     }
 }
+
+#if LBM_WALK_LAG
+// The walk with one barrier per chunk.  Iteration k takes chunk k (moments,
+// fields, side items) and, in the same phase, the normals of chunk k - 1,
+// whose fields the previous iteration's barrier published; after the barrier
+// it updates the rows of chunk k - 1 (those walk updates in its iteration
+// k - 1), from the moments each thread parked in iteration k - 1 (the top
+// two rows' one iteration earlier, through the carry).  Rows written in
+// iteration k + 1 before its barrier (fields up to Y + 2 TY + 2, normals from
+// Y - 1) and rows read by iteration k's update (from Y - TY - 3) span 3 TY + 6
+// rows of the window.  One stage.  The 16-bit kernel, whose warps waited at
+// its two barriers for the side columns' rest-moment gathers, runs 5 % faster
+// this way; for the FP32 kernel the parked moments cost more than the barrier.
+template <int S, int SLOTS, class Stage, class Out>
+__device__ __forceinline__ void walk_lag(const LbmDev& d, const Strip& sp, Stage& stg, Window<SLOTS>& W,
+                                         Park& park, uint64_t* bars, int* __restrict__ err,
+                                         const Out& out)
+{
+    static_assert(S == 1 && SLOTS >= 3 * TY + 6, "one stage and a window of 3 TY + 6 rows");
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * TX + tx;
+    if (tid == 0) mbar_init(smem_addr(&bars[0]), 1);
+    __syncthreads();
+    // last chunk this strip loads
+    const int kload = d.walls ? sp.c1 - 1 : sp.klast;
+    if (tid == 0) stg.issue(sp.kfirst, 0, smem_addr(&bars[0]));
+    uint32_t parity = 0;
+    const int rb = (ty + TY - 2) % TY;   // chunk row whose moments this thread computes
+    for (int k = sp.kfirst; k <= sp.klast + 1; ++k) {
+        const bool have = k <= kload;
+        const int Y = d.y0 + k * TY;   // unwrapped row of chunk row 0
+        bool ok = true;
+        if (have) {
+            ok = mbar_wait_bounded(smem_addr(&bars[0]), parity);
+            parity ^= 1u;
+            // (a thread whose wait gave up computes from an incomplete stage;
+            // only shared memory is written before the check below)
+            const int r = Y + rb;
+            const int phys = phys_row(d, r);
+            if (tx < sp.w) {
+                const Mom mc = stg.own_moments(0, rb, tx, phys);
+                put_fields(d, W, r, phys, tx, mc.f.s(), mc.g.s(), mc.h.s(), mc.q.s(), true);
+                park.put(k & 1, tid, mc);
+            }
+            if (tid >= NT - kSideItems) {
+                int item, rr;
+                Stage::side_slot(tid - (NT - kSideItems), item, rr);
+                stg.side_item(0, item, rr, phys_row(d, Y + rr), Y + rr, W);
+            }
+        }
+        if (k > sp.kfirst) normals_rows(W, Y - TY - 1, tid);
+        if (__syncthreads_or(!ok)) {
+            // a copy did not arrive in time: report it, and keep the block
+            // resident for one more bounded wait so that no transfer into its
+            // shared memory outlives it
+            if (tid == 0) {
+                atomicExch(err, 1);
+                mbar_wait_bounded(smem_addr(&bars[0]), parity ^ 1u);
+            }
+            return;
+        }
+        // the stage is consumed: refill it
+        if (tid == 0 && k + 1 <= kload) stg.issue(k + 1, 0, smem_addr(&bars[0]));
+        const int j = k - 1;   // the chunk whose rows this iteration updates
+        if (j < sp.kfirst) continue;
+        const bool have_j = j <= kload;
+        const int Yj = Y - TY;
+        Mom m{};
+        if (ty < 2) {
+            // the chunk's top two rows (TY - 2, TY - 1) are updated one
+            // iteration later; this one updates those of chunk j - 1
+            m = W.carry[ty][tx];
+            if (have_j && tx < sp.w) W.carry[ty][tx] = park.get(j & 1, tid);
+        } else if (have_j && tx < sp.w) {
+            m = park.get(j & 1, tid);
+        }
+        if (j >= sp.c0) {
+            // window row Yj - 2 + ty: chunk j - 1's top rows (ty < 2) or
+            // chunk j's row ty - 2
+            const int r = Yj - 2 + ty;
+            const int y = phys_row(d, r);
+            const bool fluid = !d.walls || (y >= 1 && y <= d.ny - 2);
+            if (tx < sp.w && fluid && (ty < 2 || have_j))
+                update_node(d, W, m, tx, r, sp.x0 + tx, y, out);
+        }
+    }
+}
+#endif
 
 // ---- FP32 stage -------------------------------------------------------------------------
 
@@ -1064,9 +1185,15 @@ __global__ void __launch_bounds__(NT, BPS) stream16_kernel(const __grid_constant
     if (sp.c0 >= sp.c1) return;
     Stage16<T16, S, SLOTS> stg{sm, d, sp, &args.tmap[s], &args.tside[s], &args.tmom[s],
                                static_cast<const float4*>(args.msrc[s])};
+#if LBM_WALK_LAG
+    walk_lag<S, SLOTS>(d, sp, stg, sm.win, sm.park, sm.bar, args.err[s],
+                       Out16<T16>{static_cast<uint32_t*>(args.dst[s]),
+                                  static_cast<float4*>(args.mdst[s]), d.nx * d.ny});
+#else
     walk<S, SLOTS>(d, sp, stg, sm.win, sm.bar, args.err[s],
                    Out16<T16>{static_cast<uint32_t*>(args.dst[s]), static_cast<float4*>(args.mdst[s]),
                               d.nx * d.ny});
+#endif
 }
 
 // Kernel configurations: one stage for either storage, refilled once the
